@@ -1,0 +1,410 @@
+/*
+ * vp_oracle.c -- plain, serial, FP64 CPU oracle of the phase-space-conserving
+ * Vlasov step (Edelen & Webb, "A Vlasov Algorithm Derived from Phase Space
+ * Conservation").
+ *
+ * TEST INFRASTRUCTURE ONLY. Nothing in the library's product path may link,
+ * load or call this file; only the tests, the smoke check and the benchmark's
+ * CPU-baseline leg do. It shares no code with the CUDA path.
+ *
+ * What one step computes (Sec. III, in the paper's order):
+ *   1. every mesh node k = (x_k, p_k) is pushed one step h by a particle pusher
+ *      (Sec. II; leapfrog / exact rotation / FEL drift-kick-drift);
+ *   2. the right-hand side of the Galerkin equation is formed,
+ *        r_j' = sum_k Delta_{k j'} w_k,
+ *      where Delta_{k j'} is the overlap integral of the shifted basis function
+ *      of node k with the unshifted basis function of node j' (Sec. III, the
+ *      definition of Delta). For a symmetric 1-D basis that integral is the
+ *      autoconvolution of the basis evaluated at the offset, times the cell
+ *      size, so Delta is written out in closed form:
+ *        box (top-hat) basis  ->  h * tent(offset / h)
+ *        tent basis           ->  h * B3(offset / h)   (cubic B-spline)
+ *   3. the mass-matrix equation  Lambda w_fin = r  is solved (Sec. III, the
+ *      update equation). Lambda is the overlap matrix of the unshifted basis:
+ *        box basis  ->  Lambda = hx hp I (orthogonal, Sec. III)
+ *        tent basis ->  Lambda = (hx Tx) (x) (hp Tp),  T = tridiag(1/6, 2/3, 1/6)
+ *      cyclic along the periodic coordinate, the plain (truncated) Toeplitz
+ *      matrix along the open momentum axis (Sec. IV: periodic coordinates,
+ *      open momenta). LUMPED replaces Lambda by its row sums (hx hp I).
+ *   4. for the FEL model the bunching <exp(-i theta)> of the new weights drives
+ *      the field amplitude A (Sec. IV.B, dA/dz = <exp(-i Phi)>).
+ *
+ * Deposits that land on momentum rows outside the grid are lost (open
+ * boundaries, Sec. IV) and accumulated in a lost-weight counter.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fPIC -shared vp_oracle.c -lm
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int nx, np;
+    double x0, x1, p0, p1;
+} or_grid;
+
+typedef struct {
+    int kind;       /* 0 leapfrog KDK, 1 exact rotation, 2 FEL DKD */
+    int potential;  /* 0 free, 1 pendulum V=-s cos x, 2 harmonic V=w^2 x^2/2 */
+    double v_sign;
+    double omega;
+    double dt;
+} or_pusher;
+
+enum { OR_KDK = 0, OR_ROT = 1, OR_FEL = 2 };
+enum { OR_FREE = 0, OR_PEND = 1, OR_HARM = 2 };
+enum { OR_TENT = 0, OR_CUBIC = 1 };
+enum { OR_GALERKIN = 0, OR_LUMPED = 1 };
+
+#define OR_NMOM 14
+
+static double grid_hx(const or_grid *g) { return (g->x1 - g->x0) / g->nx; }
+static double grid_hp(const or_grid *g) { return (g->p1 - g->p0) / (g->np - 1); }
+
+/* ---------------------------------------------------------------- pushers */
+
+/* dV/dx for the Hamiltonian H = p^2/2 + V(x) (Sec. II). */
+static double dVdx(const or_pusher *pu, double x)
+{
+    switch (pu->potential) {
+    case OR_PEND: return pu->v_sign * sin(x);
+    case OR_HARM: return pu->omega * pu->omega * x;
+    default: return 0.0;
+    }
+}
+
+static double potential(const or_pusher *pu, double x)
+{
+    switch (pu->potential) {
+    case OR_PEND: return -pu->v_sign * cos(x);
+    case OR_HARM: return 0.5 * pu->omega * pu->omega * x * x;
+    default: return 0.0;
+    }
+}
+
+/*
+ * One step of the flow for a single phase-space point (Sec. II: the flow is
+ * approximated by a particle pusher over the step h).
+ *   KDK (second-order symplectic leapfrog, Sec. IV.A):
+ *       p_half = p - h/2 V'(x);  x' = x + h p_half;  p' = p_half - h/2 V'(x')
+ *   exact rotation (linear oscillator advanced analytically, Sec. IV.A):
+ *       phase advance omega h.
+ *   FEL drift-kick-drift of d theta/dz = eta, d eta/dz = -(A e^{i theta} + cc)
+ *   (Sec. IV.B with detuning and space charge set to zero), A = A^{n+1/2}.
+ */
+void or_push(const or_pusher *pu, double a_re, double a_im,
+             double x, double p, double *xo, double *po)
+{
+    const double h = pu->dt;
+    if (pu->kind == OR_KDK) {
+        double ph = p - 0.5 * h * dVdx(pu, x);
+        double xn = x + h * ph;
+        *po = ph - 0.5 * h * dVdx(pu, xn);
+        *xo = xn;
+    } else if (pu->kind == OR_ROT) {
+        double ph = pu->omega * h;
+        double c = cos(ph), s = sin(ph);
+        *xo = x * c + p * s / pu->omega;
+        *po = -pu->omega * x * s + p * c;
+    } else {
+        double th = x + 0.5 * h * p;
+        /* A e^{i th} + c.c. = 2 Re(A e^{i th}) */
+        double re = a_re * cos(th) - a_im * sin(th);
+        double pn = p - h * 2.0 * re;
+        *xo = th + 0.5 * h * pn;
+        *po = pn;
+    }
+}
+
+void or_push_many(const or_pusher *pu, double a_re, double a_im, long n,
+                  const double *x, const double *p, double *xo, double *po)
+{
+    for (long k = 0; k < n; ++k)
+        or_push(pu, a_re, a_im, x[k], p[k], &xo[k], &po[k]);
+}
+
+/* ------------------------------------------------- overlap-integral kernels */
+
+/* autoconvolution of the unit top-hat: the tent */
+static double k_tent(double d)
+{
+    d = fabs(d);
+    return d < 1.0 ? 1.0 - d : 0.0;
+}
+
+/* autoconvolution of the unit tent: the cubic B-spline */
+static double k_b3(double d)
+{
+    d = fabs(d);
+    if (d < 1.0) return 2.0 / 3.0 - d * d + 0.5 * d * d * d;
+    if (d < 2.0) {
+        double e = 2.0 - d;
+        return e * e * e / 6.0;
+    }
+    return 0.0;
+}
+
+static long mod_l(long a, long n)
+{
+    long r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+/* ------------------------------------------------------ mass-matrix solves */
+
+/* Thomas algorithm: sub a, diag b, super c (constant a, c; diag per row). */
+static void thomas(int n, double a, const double *bdiag, double c,
+                   double *d, double *cp)
+{
+    double beta = bdiag[0];
+    cp[0] = c / beta;
+    d[0] = d[0] / beta;
+    for (int i = 1; i < n; ++i) {
+        beta = bdiag[i] - a * cp[i - 1];
+        cp[i] = c / beta;
+        d[i] = (d[i] - a * d[i - 1]) / beta;
+    }
+    for (int i = n - 2; i >= 0; --i)
+        d[i] -= cp[i] * d[i + 1];
+}
+
+/*
+ * Cyclic symmetric tridiagonal solve (diag b, off-diagonals and corners a),
+ * by the Sherman-Morrison correction of a plain tridiagonal solve.
+ * Requires n >= 3. d is overwritten with the solution. work: 4n doubles.
+ */
+static void cyclic_solve(int n, double a, double b, double *d, double *work)
+{
+    double *bd = work, *z = work + n, *cp = work + 2 * n;
+    const double gamma = -b;
+    for (int i = 0; i < n; ++i) bd[i] = b;
+    bd[0] = b - gamma;
+    bd[n - 1] = b - a * a / gamma;
+    /* T y = d */
+    thomas(n, a, bd, a, d, cp);
+    /* T z = u,  u = (gamma, 0, ..., 0, a) */
+    memset(z, 0, sizeof(double) * n);
+    z[0] = gamma;
+    z[n - 1] = a;
+    thomas(n, a, bd, a, z, cp);
+    /* v = (1, 0, ..., 0, a / gamma) */
+    double vy = d[0] + (a / gamma) * d[n - 1];
+    double vz = z[0] + (a / gamma) * z[n - 1];
+    double fac = vy / (1.0 + vz);
+    for (int i = 0; i < n; ++i) d[i] -= fac * z[i];
+}
+
+/*
+ * Solve Lambda w = r in place, Lambda = (hx Tx) (x) (hp Tp), Tx cyclic
+ * tridiag(1/6, 2/3, 1/6) along x (rows of the [np][nx] array), Tp the
+ * np x np tridiag(1/6, 2/3, 1/6) along p (columns).
+ */
+void or_mass_solve(const or_grid *g, double *r)
+{
+    const int nx = g->nx, np = g->np;
+    const double hx = grid_hx(g), hp = grid_hp(g);
+    int nmax = nx > np ? nx : np;
+    double *work = (double *)malloc(sizeof(double) * 5 * nmax);
+    double *col = work + 4 * nmax;
+    /* x: cyclic, matrix hx * tridiag(1/6, 2/3, 1/6) */
+    for (int j = 0; j < np; ++j)
+        cyclic_solve(nx, hx / 6.0, 2.0 * hx / 3.0, r + (long)j * nx, work);
+    /* p: open, matrix hp * tridiag(1/6, 2/3, 1/6) */
+    double *bd = work;
+    double *cp = work + nmax;
+    for (int i = 0; i < nx; ++i) {
+        for (int j = 0; j < np; ++j) {
+            col[j] = r[(long)j * nx + i];
+            bd[j] = 2.0 * hp / 3.0;
+        }
+        thomas(np, hp / 6.0, bd, hp / 6.0, col, cp);
+        for (int j = 0; j < np; ++j) r[(long)j * nx + i] = col[j];
+    }
+    free(work);
+}
+
+/* ------------------------------------------------------------------ step */
+
+/*
+ * One step w_in -> w_out.
+ * fel (FEL only, else may be NULL): [A_re, A_im, b_re, b_im] at step n on
+ * entry, at step n+1 on exit, where b = <exp(-i theta)> of the weights.
+ * lost (may be NULL): accumulates the weight deposited outside the momentum
+ * range, in units of sum(w).
+ * Returns 0 on success, nonzero on bad arguments.
+ */
+int or_step(const or_grid *g, int basis, int projection, const or_pusher *pu,
+            double *fel, const double *w_in, double *w_out, double *lost)
+{
+    const int nx = g->nx, np = g->np;
+    if (nx < 3 || np < 2) return 1;
+    const double hx = grid_hx(g), hp = grid_hp(g);
+    const long n = (long)nx * np;
+    double a_re = 0.0, a_im = 0.0;
+    if (pu->kind == OR_FEL) {
+        if (!fel) return 2;
+        /* A^{n+1/2} = A^n + h/2 b^n */
+        a_re = fel[0] + 0.5 * pu->dt * fel[2];
+        a_im = fel[1] + 0.5 * pu->dt * fel[3];
+    }
+    const double radius = (basis == OR_TENT) ? 1.0 : 2.0;
+    double lost_acc = 0.0;
+    memset(w_out, 0, sizeof(double) * n);
+
+    /* r_j' = sum_k Delta_{k j'} w_k */
+    for (int j = 0; j < np; ++j) {
+        const double p = g->p0 + j * hp;
+        for (int i = 0; i < nx; ++i) {
+            const double w = w_in[(long)j * nx + i];
+            if (w == 0.0) continue;
+            const double x = g->x0 + i * hx;
+            double xf, pf;
+            or_push(pu, a_re, a_im, x, p, &xf, &pf);
+            const double u = (xf - g->x0) / hx;   /* pushed position, cell units */
+            const double v = (pf - g->p0) / hp;
+            const long c_lo = (long)ceil(u - radius), c_hi = (long)floor(u + radius);
+            const long r_lo = (long)ceil(v - radius), r_hi = (long)floor(v + radius);
+            for (long rr = r_lo; rr <= r_hi; ++rr) {
+                const double kp = hp * (basis == OR_TENT ? k_tent(rr - v) : k_b3(rr - v));
+                if (kp == 0.0) continue;
+                for (long cc = c_lo; cc <= c_hi; ++cc) {
+                    const double kx = hx * (basis == OR_TENT ? k_tent(cc - u) : k_b3(cc - u));
+                    const double contrib = kx * kp * w;
+                    if (rr < 0 || rr >= np) {
+                        lost_acc += contrib;
+                        continue;
+                    }
+                    w_out[rr * nx + mod_l(cc, nx)] += contrib;
+                }
+            }
+        }
+    }
+    /* Lambda w_fin = r */
+    if (basis == OR_CUBIC && projection == OR_GALERKIN) {
+        or_mass_solve(g, w_out);
+    } else {
+        const double inv = 1.0 / (hx * hp);
+        for (long k = 0; k < n; ++k) w_out[k] *= inv;
+    }
+    if (lost) *lost += lost_acc / (hx * hp);
+
+    if (pu->kind == OR_FEL) {
+        /* b = <exp(-i theta)> over the new weights; A^{n+1} = A^{n+1/2} + h/2 b */
+        double s = 0.0, sc = 0.0, ss = 0.0;
+        for (int j = 0; j < np; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const double w = w_out[(long)j * nx + i];
+                const double th = g->x0 + i * hx;
+                s += w;
+                sc += w * cos(th);
+                ss += w * sin(th);
+            }
+        fel[2] = sc / s;
+        fel[3] = -ss / s;
+        fel[0] = a_re + 0.5 * pu->dt * fel[2];
+        fel[1] = a_im + 0.5 * pu->dt * fel[3];
+    }
+    return 0;
+}
+
+/* FEL: b = <exp(-i theta)> of weights w (used to start the field recursion). */
+void or_bunching(const or_grid *g, const double *w, double *b_re, double *b_im)
+{
+    const double hx = grid_hx(g);
+    double s = 0.0, sc = 0.0, ss = 0.0;
+    for (int j = 0; j < g->np; ++j)
+        for (int i = 0; i < g->nx; ++i) {
+            const double ww = w[(long)j * g->nx + i];
+            const double th = g->x0 + i * hx;
+            s += ww;
+            sc += ww * cos(th);
+            ss += ww * sin(th);
+        }
+    *b_re = sc / s;
+    *b_im = -ss / s;
+}
+
+/*
+ * nsteps steps, ping-ponging between w (in/out) and a scratch array.
+ * hist (may be NULL): 2 doubles per step, A^{n+1} (re, im) after each step.
+ */
+int or_run(const or_grid *g, int basis, int projection, const or_pusher *pu,
+           double *fel, double *w, long nsteps, double *lost, double *hist)
+{
+    const long n = (long)g->nx * g->np;
+    double *tmp = (double *)malloc(sizeof(double) * n);
+    if (!tmp) return 3;
+    for (long s = 0; s < nsteps; ++s) {
+        int rc = or_step(g, basis, projection, pu, fel, w, tmp, lost);
+        if (rc) { free(tmp); return rc; }
+        memcpy(w, tmp, sizeof(double) * n);
+        if (hist && pu->kind == OR_FEL) {
+            hist[2 * s] = fel[0];
+            hist[2 * s + 1] = fel[1];
+        }
+    }
+    free(tmp);
+    return 0;
+}
+
+/*
+ * Diagnostics of the weights (Sec. IV: sum of weights, entropy).
+ * out[0]  sum w                     out[7]  energy: <H> (Hamiltonian pushers)
+ * out[1]  mass = sum w hx hp                or <p> + |A|^2 (FEL)
+ * out[2]  <x>                       out[8]  trapped mass, H < max V (pendulum)
+ * out[3]  <p>                       out[9]  entropy -sum_{w>0} w ln w hx hp
+ * out[4]  var x                     out[10] negative mass sum_{w<0} w hx hp
+ * out[5]  var p                     out[11] b_re = Re <exp(-i x)>
+ * out[6]  cov(x, p)                 out[12] b_im
+ *                                   out[13] max |w|
+ * a (FEL, may be NULL): [A_re, A_im].
+ */
+void or_moments(const or_grid *g, const or_pusher *pu, const double *w,
+                const double *a, double *out)
+{
+    const double hx = grid_hx(g), hp = grid_hp(g);
+    double s = 0, sx = 0, sp = 0, sxx = 0, spp = 0, sxp = 0, sh = 0, trapped = 0;
+    double ent = 0, neg = 0, sc = 0, ss = 0, wmax = 0;
+    const double hsep = fabs(pu->v_sign);
+    for (int j = 0; j < g->np; ++j) {
+        const double p = g->p0 + j * hp;
+        for (int i = 0; i < g->nx; ++i) {
+            const double x = g->x0 + i * hx;
+            const double ww = w[(long)j * g->nx + i];
+            const double hh = 0.5 * p * p + potential(pu, x);
+            s += ww;
+            sx += ww * x;
+            sp += ww * p;
+            sxx += ww * x * x;
+            spp += ww * p * p;
+            sxp += ww * x * p;
+            sh += ww * hh;
+            if (pu->kind == OR_KDK && pu->potential == OR_PEND && hh < hsep) trapped += ww;
+            if (ww > 0) ent -= ww * log(ww);
+            if (ww < 0) neg += ww;
+            sc += ww * cos(x);
+            ss += ww * sin(x);
+            if (fabs(ww) > wmax) wmax = fabs(ww);
+        }
+    }
+    const double mx = sx / s, mp = sp / s;
+    out[0] = s;
+    out[1] = s * hx * hp;
+    out[2] = mx;
+    out[3] = mp;
+    out[4] = sxx / s - mx * mx;
+    out[5] = spp / s - mp * mp;
+    out[6] = sxp / s - mx * mp;
+    if (pu->kind == OR_FEL)
+        out[7] = mp + (a ? a[0] * a[0] + a[1] * a[1] : 0.0);
+    else
+        out[7] = sh / s;
+    out[8] = trapped * hx * hp;
+    out[9] = ent * hx * hp;
+    out[10] = neg * hx * hp;
+    out[11] = sc / s;
+    out[12] = -ss / s;
+    out[13] = wmax;
+}
+
+int or_nmom(void) { return OR_NMOM; }
