@@ -1,0 +1,177 @@
+/*
+ * vlasov.h -- C ABI of the GB300 phase-space-conserving Vlasov step.
+ *
+ * Method (Edelen & Webb, "A Vlasov Algorithm Derived from Phase Space
+ * Conservation"): the density is a set of weights w on a tensor-product mesh
+ * of basis functions (Sec. III, the basis expansion). Each step every mesh node
+ * is pushed as a particle over the step h (Sec. II), and the shifted basis
+ * functions are projected back onto the mesh (Sec. III, the Galerkin equation
+ * Lambda w_fin = Delta^T w_in and its update w_fin = Lambda^{-1} Delta^T w_in).
+ * For the 1-D FEL model the bunching <exp(-i theta)> of the weights drives
+ * the field amplitude A (Sec. IV.B, dA/dz = <exp(-i Phi)>).
+ *
+ * Conventions shared by every call:
+ *   - the mesh is row-major [np][nx], x (the coordinate) fastest;
+ *     x_i = x0 + i (x1 - x0) / nx is periodic (Sec. IV: periodic coordinates),
+ *     p_j = p0 + j (p1 - p0) / (np - 1) is open, end nodes included (Sec. IV:
+ *     open momenta; weight pushed beyond p0 or p1 is lost and counted);
+ *   - all device memory is owned by the caller: vp_workspace_size() says how
+ *     much, vp_create() receives it. The library allocates no device memory.
+ *   - every call returns a vp_status; no call throws. vp_last_error() gives a
+ *     human-readable reason for the last failure on that simulation.
+ *   - calls on one vp_sim are not thread-safe; use one host thread per sim.
+ *   - work is enqueued on the stream given in vp_opts.stream (a cudaStream_t,
+ *     NULL = legacy default stream); calls that return host data synchronise
+ *     that stream.
+ */
+#ifndef VLASOV_H
+#define VLASOV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum vp_status {
+    VP_OK = 0,
+    VP_ERR_ARG = 1,         /* invalid argument (NULL pointer, bad size or enum) */
+    VP_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed */
+    VP_ERR_WORKSPACE = 3,   /* workspace NULL, misaligned or smaller than required */
+    VP_ERR_NONFINITE = 4,   /* a step produced a NaN or infinity (device flag) */
+    VP_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (device flag) */
+    VP_ERR_STATE = 6,       /* call out of order (e.g. vp_step before vp_set_f) */
+    VP_ERR_UNSUPPORTED = 7  /* valid request this build cannot serve (size limits) */
+} vp_status;
+
+/* Deposition kernel = autoconvolution of the basis (Sec. III, Delta). */
+enum {
+    VP_BASIS_TENT = 0,           /* top-hat basis: tent deposit, Lambda = h I (orthogonal) */
+    VP_BASIS_CUBIC_BSPLINE = 1   /* tent basis: cubic B-spline deposit, Lambda = h tridiag(1/6,2/3,1/6) */
+};
+
+/* Particle pusher for the node flow (Sec. II; examples of Sec. IV). */
+enum {
+    VP_PUSH_LEAPFROG_KDK = 0,    /* kick-drift-kick, H = p^2/2 + V(x) */
+    VP_PUSH_EXACT_ROTATION = 1,  /* linear oscillator advanced analytically (Sec. IV.A) */
+    VP_PUSH_FEL_DKD = 2          /* 1-D FEL, drift-kick-drift with A^{n+1/2} (Sec. IV.B) */
+};
+
+enum {
+    VP_POT_FREE = 0,       /* V = 0 */
+    VP_POT_PENDULUM = 1,   /* V = -v_sign cos x (v_sign = -1: the paper's H = p^2/2 + cos x) */
+    VP_POT_HARMONIC = 2    /* V = omega^2 x^2 / 2 */
+};
+
+enum { VP_FP32 = 0, VP_FP64 = 1 };
+
+/* Treatment of Lambda for the cubic B-spline deposit (Sec. III update equation). */
+enum {
+    VP_PROJ_GALERKIN = 0,  /* solve Lambda w_fin = Delta^T w_in exactly */
+    VP_PROJ_LUMPED = 1     /* Lambda replaced by its row sum h I (no solve) */
+};
+
+/* Step-kernel choice. */
+enum {
+    VP_KERNEL_AUTO = 0,     /* planner's choice (tiled) */
+    VP_KERNEL_TILED = 1,    /* destination tiles in shared memory, one coalesced store */
+    VP_KERNEL_SCATTER = 2   /* one thread per source node, global atomics (reference path) */
+};
+
+typedef struct vp_grid {
+    int32_t nx, np;        /* nodes along x (>= 4) and p (>= 4) */
+    double x0, x1;         /* periodic coordinate range [x0, x1) */
+    double p0, p1;         /* open momentum range [p0, p1], end nodes included */
+} vp_grid;
+
+typedef struct vp_pusher {
+    int32_t kind;          /* VP_PUSH_* */
+    int32_t potential;     /* VP_POT_* (leapfrog / rotation) */
+    double v_sign;         /* pendulum amplitude and sign, V = -v_sign cos x */
+    double omega;          /* harmonic frequency */
+    double dt;             /* step h */
+    double a0_re, a0_im;   /* FEL: field amplitude A at tau = 0 */
+} vp_pusher;
+
+typedef struct vp_opts {
+    int32_t precision;     /* VP_FP32 or VP_FP64: type of w, the push and the deposit */
+    int32_t projection;    /* VP_PROJ_* (cubic B-spline only) */
+    int32_t kernel;        /* VP_KERNEL_* */
+    int32_t tile_x;        /* tiled kernel: destination tile width (0 = planner) */
+    int32_t tile_p;        /* tiled kernel: destination tile height (0 = planner) */
+    int32_t history_cap;   /* FEL field-history ring capacity in steps (0 = 4096) */
+    void *stream;          /* cudaStream_t for all work of this sim (NULL = default stream) */
+} vp_opts;
+
+/* FP64 diagnostics (Sec. IV: sum of weights, entropy; Sec. IV.B: field). */
+typedef struct vp_moments_t {
+    double sum_w;          /* sum of weights */
+    double mass;           /* sum_w * hx * hp */
+    double mean_x, mean_p;
+    double var_x, var_p, cov_xp;
+    double energy;         /* <H> for Hamiltonian pushers; <p> + |A|^2 for the FEL */
+    double trapped;        /* mass with H < max V (pendulum), else 0 */
+    double entropy;        /* -sum_{w>0} w ln w * hx * hp */
+    double neg_mass;       /* sum_{w<0} w * hx * hp */
+    double b_re, b_im;     /* <exp(-i x)> of the weights */
+    double max_abs_w;
+    double lost_mass;      /* deposit pushed beyond the momentum range, times hx hp, cumulative */
+    double a_re, a_im;     /* FEL field A at the current step */
+    double tau;            /* step * dt */
+    int64_t step;
+} vp_moments_t;
+
+typedef struct vp_sim vp_sim;
+
+/* Bytes of device workspace vp_create() needs for this configuration. */
+vp_status vp_workspace_size(const vp_grid *grid, int32_t basis, const vp_pusher *pusher,
+                            const vp_opts *opts, size_t *bytes);
+
+/*
+ * Create a simulation. workspace: caller-owned device memory, 256-byte aligned,
+ * at least vp_workspace_size() bytes, kept alive until vp_destroy(). The
+ * geometry tables of the push are built on the device here (Sec. II flow).
+ */
+vp_status vp_create(const vp_grid *grid, int32_t basis, const vp_pusher *pusher,
+                    const vp_opts *opts, void *workspace, size_t workspace_bytes, vp_sim **out);
+
+/* Set the weights from host memory ([np][nx], dtype VP_FP32 / VP_FP64, n = nx*np).
+ * Converts to the sim's precision; pinned host memory makes the copy asynchronous
+ * when dtype equals the sim precision. Resets step, tau, lost mass and A = A0. */
+vp_status vp_set_f(vp_sim *sim, const void *host, int32_t dtype, size_t n);
+/* Same from device memory (device-to-device on the sim's stream). */
+vp_status vp_set_f_device(vp_sim *sim, const void *dev, int32_t dtype, size_t n);
+
+/* Advance n steps: push + deposit (+ Lambda^{-1}) (+ FEL bunching and field). Asynchronous. */
+vp_status vp_step(vp_sim *sim, int32_t n);
+
+/* Copy the weights out ([np][nx] in dtype). vp_get_f synchronises the stream. */
+vp_status vp_get_f(vp_sim *sim, void *host, int32_t dtype, size_t n);
+vp_status vp_get_f_device(vp_sim *sim, void *dev, int32_t dtype, size_t n);
+
+/* FP64 reductions over the current weights; synchronises. */
+vp_status vp_moments(vp_sim *sim, vp_moments_t *out);
+
+/* FEL: A after each step (re, im pairs), oldest first, up to max_entries of the
+ * most recent history_cap steps; *count receives the number written. */
+vp_status vp_field_history(vp_sim *sim, double *re_im, size_t max_entries, size_t *count);
+
+/* Synchronise the sim's stream and report device-side error flags. */
+vp_status vp_sync(vp_sim *sim);
+
+/* Redirect later work to another stream (no synchronisation is implied). */
+vp_status vp_set_stream(vp_sim *sim, void *stream);
+
+/* Device pointer of the current weights (valid until the next vp_step). */
+vp_status vp_state_device(vp_sim *sim, void **dev);
+
+void vp_destroy(vp_sim *sim);
+const char *vp_last_error(const vp_sim *sim);
+const char *vp_status_string(vp_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VLASOV_H */

@@ -1,0 +1,662 @@
+// vp_api.cu -- host side of the C ABI declared in include/vlasov.h: argument
+// checks, the planner (tile shape, workspace layout, source-window bounds), and
+// the per-step launch sequence
+//   push + deposit  ->  [Lambda^{-1}: x solve, p solve]  ->  [FEL field update]
+// on the caller's stream. The library allocates no device memory: every device
+// buffer is carved out of the caller's workspace.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "vp_internal.h"
+
+using namespace vp;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kDefaultHist = 4096;
+constexpr size_t kMaxSmem = 220 * 1024;
+constexpr int kMoutLen = 32;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+    size_t f0, f1, tmp, col, row, rowb, vcb, csx, ucol, vcol, piv, state, hist, lost, part, mpart,
+        mout, err, total;
+};
+
+struct Plan {
+    Geometry g;
+    int precision, projection, kernel, tx, tp, ntx, ntp, hist_cap, nlost, npart, nmblk, nblk;
+    bool galerkin, fel;
+    Layout L;
+};
+
+vp_status fail(char *msg, vp_status st, const char *fmt, ...)
+{
+    if (msg) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(msg, 512, fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+bool finite(double v) { return isfinite(v) != 0; }
+
+vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, const vp_opts *opts,
+                    Plan *P, char *msg)
+{
+    if (!grid || !pu || !opts) return fail(msg, VP_ERR_ARG, "NULL grid, pusher or opts");
+    if (grid->nx < 4 || grid->np < 4)
+        return fail(msg, VP_ERR_ARG, "grid needs nx >= 4 and np >= 4 (got %d x %d)", grid->nx,
+                    grid->np);
+    if ((double)grid->nx * grid->np > 2147483647.0)
+        return fail(msg, VP_ERR_UNSUPPORTED, "nx * np must stay below 2^31");
+    if (!finite(grid->x0) || !finite(grid->x1) || !finite(grid->p0) || !finite(grid->p1) ||
+        !(grid->x1 > grid->x0) || !(grid->p1 > grid->p0))
+        return fail(msg, VP_ERR_ARG, "grid ranges must be finite with x1 > x0 and p1 > p0");
+    if (basis != VP_BASIS_TENT && basis != VP_BASIS_CUBIC_BSPLINE)
+        return fail(msg, VP_ERR_ARG, "unknown basis %d", basis);
+    if (pu->kind < 0 || pu->kind > 2) return fail(msg, VP_ERR_ARG, "unknown pusher kind %d", pu->kind);
+    if (pu->potential < 0 || pu->potential > 2)
+        return fail(msg, VP_ERR_ARG, "unknown potential %d", pu->potential);
+    if (!finite(pu->dt) || !finite(pu->v_sign) || !finite(pu->omega) || !finite(pu->a0_re) ||
+        !finite(pu->a0_im))
+        return fail(msg, VP_ERR_ARG, "pusher parameters must be finite");
+    if (opts->precision != VP_FP32 && opts->precision != VP_FP64)
+        return fail(msg, VP_ERR_ARG, "unknown precision %d", opts->precision);
+    if (opts->projection != VP_PROJ_GALERKIN && opts->projection != VP_PROJ_LUMPED)
+        return fail(msg, VP_ERR_ARG, "unknown projection %d", opts->projection);
+    if (opts->kernel < 0 || opts->kernel > 2) return fail(msg, VP_ERR_ARG, "unknown kernel %d", opts->kernel);
+    if (opts->tile_x < 0 || opts->tile_p < 0 || opts->history_cap < 0)
+        return fail(msg, VP_ERR_ARG, "tile sizes and history capacity must be >= 0");
+
+    Geometry &g = P->g;
+    memset(&g, 0, sizeof(g));
+    g.nx = grid->nx;
+    g.np = grid->np;
+    g.x0 = grid->x0;
+    g.x1 = grid->x1;
+    g.p0 = grid->p0;
+    g.p1 = grid->p1;
+    g.hx = (grid->x1 - grid->x0) / grid->nx;
+    g.hp = (grid->p1 - grid->p0) / (grid->np - 1);
+    g.basis = basis;
+    g.kind = pu->kind;
+    g.potential = pu->potential;
+    g.projection = opts->projection;
+    g.v_sign = pu->v_sign;
+    g.omega = pu->omega;
+    g.dt = pu->dt;
+    const double h = pu->dt;
+    const bool pend = pu->kind == VP_PUSH_LEAPFROG_KDK && pu->potential == VP_POT_PENDULUM;
+    P->fel = pu->kind == VP_PUSH_FEL_DKD;
+    if (pend || P->fel) {
+        const double L = grid->x1 - grid->x0, per = L / (2.0 * M_PI);
+        if (fabs(per - rint(per)) > 1e-9 * per || rint(per) < 1.0)
+            return fail(msg, VP_ERR_ARG,
+                        "pendulum and FEL need a coordinate period that is a multiple of 2 pi");
+    }
+    if ((pu->kind == VP_PUSH_EXACT_ROTATION ||
+         (pu->kind == VP_PUSH_LEAPFROG_KDK && pu->potential == VP_POT_HARMONIC)) &&
+        !(pu->omega > 0.0))
+        return fail(msg, VP_ERR_ARG, "harmonic motion needs omega > 0");
+    if (pend) {
+        g.KV = -(h / (2.0 * g.hp));
+        g.alpha0 = pu->v_sign;
+        g.a_pad = 0.5 * h * h * fabs(pu->v_sign);
+    } else if (P->fel) {
+        g.KU = -(h * h / g.hx);
+        g.KV = -(2.0 * h / g.hp);
+    }
+
+    P->precision = opts->precision;
+    P->projection = opts->projection;
+    P->galerkin = basis == VP_BASIS_CUBIC_BSPLINE && opts->projection == VP_PROJ_GALERKIN;
+    int kernel = opts->kernel;
+    if (kernel == VP_KERNEL_AUTO) {
+        kernel = VP_KERNEL_TILED;
+        if (pu->kind == VP_PUSH_EXACT_ROTATION && fabs(pu->omega * h) >= 0.5 * M_PI)
+            kernel = VP_KERNEL_SCATTER;
+    }
+    P->kernel = kernel;
+    const size_t sz = opts->precision == VP_FP64 ? 8 : 4;
+    int tx = opts->tile_x ? opts->tile_x : (opts->precision == VP_FP64 ? 64 : 128);
+    int tp = opts->tile_p ? opts->tile_p : 64;
+    tx = std::min(tx, grid->nx);
+    tp = std::min(tp, grid->np);
+    if (tx > 4096 || tp > 4096) return fail(msg, VP_ERR_ARG, "tile sides must be <= 4096");
+    if (kernel == VP_KERNEL_TILED) {
+        const size_t smem = sz == 8 ? tiled_smem_bytes<double>(tx, tp) : tiled_smem_bytes<float>(tx, tp);
+        if (smem > kMaxSmem)
+            return fail(msg, VP_ERR_UNSUPPORTED, "tile %d x %d needs %zu bytes of shared memory", tx,
+                        tp, smem);
+    }
+    if (P->galerkin) {
+        const size_t smem = (size_t)(grid->nx + grid->nx / 32 + 1) * sz;
+        if (smem > kMaxSmem)
+            return fail(msg, VP_ERR_UNSUPPORTED,
+                        "the cyclic x solve keeps a row in shared memory: nx = %d is too large",
+                        grid->nx);
+    }
+    P->tx = tx;
+    P->tp = tp;
+    P->ntx = (grid->nx + tx - 1) / tx;
+    P->ntp = (grid->np + tp - 1) / tp;
+    P->hist_cap = opts->history_cap ? opts->history_cap : kDefaultHist;
+    P->nlost = kernel == VP_KERNEL_TILED ? P->ntx * P->ntp : 1;
+    P->npart = std::max(std::max(filter_p_blocks(grid->nx, grid->np), P->ntx * P->ntp),
+                        fel_partial_blocks(grid->nx, grid->np));
+    P->nmblk = moment_blocks(grid->nx, grid->np);
+    P->nblk = (grid->nx + kColBlock - 1) / kColBlock;
+
+    const size_t N = (size_t)grid->nx * grid->np;
+    const size_t colsz = sz == 8 ? sizeof(ColEntry<double>) : sizeof(ColEntry<float>);
+    const size_t rowsz = sz == 8 ? sizeof(RowEntry<double>) : sizeof(RowEntry<float>);
+    Layout &L = P->L;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    L.f0 = take(N * sz);
+    L.f1 = take(N * sz);
+    L.tmp = take(P->galerkin ? N * sz : 0);
+    L.col = take(grid->nx * colsz);
+    L.row = take(grid->np * rowsz);
+    L.rowb = take(grid->np * sizeof(RowBound));
+    L.vcb = take(P->nblk * 2 * sizeof(double));
+    L.csx = take(grid->nx * sizeof(double2));
+    L.ucol = take(grid->nx * sizeof(double));
+    L.vcol = take(grid->nx * sizeof(double));
+    L.piv = take((2 * kPivots + 2) * sizeof(double));
+    L.state = take(ST_NSTATE * sizeof(double));
+    L.hist = take((size_t)P->hist_cap * 2 * sizeof(double));
+    L.lost = take(P->nlost * sizeof(double));
+    L.part = take((size_t)P->npart * 3 * sizeof(double));
+    L.mpart = take((size_t)P->nmblk * kNumMoments * sizeof(double));
+    L.mout = take(kMoutLen * sizeof(double));
+    L.err = take(sizeof(unsigned));
+    L.total = off;
+    return VP_OK;
+}
+
+}  // namespace
+
+struct vp_sim {
+    Plan P;
+    cudaStream_t stream;
+    char *ws;
+    int cur;
+    bool f_set;
+    double a0_re, a0_im;
+    double host_state[ST_NSTATE];
+    double host_mout[kMoutLen];
+    unsigned host_err;
+    char msg[512];
+
+    template <typename T>
+    T *ptr(size_t off) const { return reinterpret_cast<T *>(ws + off); }
+    void *f(int k) const { return ws + (k == 0 ? P.L.f0 : P.L.f1); }
+};
+
+namespace {
+
+vp_status cuda_fail(vp_sim *s, cudaError_t e, const char *what)
+{
+    return fail(s ? s->msg : nullptr, VP_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define VP_CUDA(sim, ...)                                              \
+    do {                                                               \
+        cudaError_t e_ = (__VA_ARGS__);                                \
+        if (e_ != cudaSuccess) return cuda_fail(sim, e_, #__VA_ARGS__); \
+    } while (0)
+
+template <typename T>
+StepArgs<T> step_args(vp_sim *s, const void *src, void *dst)
+{
+    const Plan &P = s->P;
+    StepArgs<T> a;
+    a.src = static_cast<const T *>(src);
+    a.dst = static_cast<T *>(dst);
+    a.col = s->ptr<ColEntry<T>>(P.L.col);
+    a.row = s->ptr<RowEntry<T>>(P.L.row);
+    a.rowb = s->ptr<RowBound>(P.L.rowb);
+    a.vcb = s->ptr<double>(P.L.vcb);
+    a.state = s->ptr<double>(P.L.state);
+    a.csx = s->ptr<double2>(P.L.csx);
+    a.tile_lost = s->ptr<double>(P.L.lost);
+    a.tile_part = s->ptr<double>(P.L.part);
+    a.err = s->ptr<unsigned>(P.L.err);
+    a.g = P.g;
+    a.tx = P.tx;
+    a.tp = P.tp;
+    a.ntx = P.ntx;
+    a.ntp = P.ntp;
+    a.fel_partials = (P.fel && !P.galerkin && P.kernel == VP_KERNEL_TILED) ? 1 : 0;
+    return a;
+}
+
+template <typename T>
+vp_status fel_bunching(vp_sim *s, const void *w, int init)
+{
+    const Plan &P = s->P;
+    double *part = s->ptr<double>(P.L.part);
+    VP_CUDA(s, launch_fel_partials<T>(static_cast<const T *>(w), P.g.nx, P.g.np,
+                                      s->ptr<double2>(P.L.csx), part, s->stream));
+    VP_CUDA(s, launch_fel_finalize(part, fel_partial_blocks(P.g.nx, P.g.np), s->ptr<double>(P.L.state),
+                                   s->ptr<double>(P.L.hist), P.hist_cap, P.g.dt, init, s->stream));
+    return VP_OK;
+}
+
+template <typename T>
+vp_status do_steps(vp_sim *s, int n)
+{
+    const Plan &P = s->P;
+    const size_t N = (size_t)P.g.nx * P.g.np;
+    double *part = s->ptr<double>(P.L.part);
+    double *state = s->ptr<double>(P.L.state);
+    unsigned *err = s->ptr<unsigned>(P.L.err);
+    for (int k = 0; k < n; ++k) {
+        void *src = s->f(s->cur), *dst = s->f(1 - s->cur);
+        StepArgs<T> a = step_args<T>(s, src, dst);
+        if (P.kernel == VP_KERNEL_TILED) {
+            VP_CUDA(s, launch_step_tiled<T>(a, s->stream));
+        } else {
+            VP_CUDA(s, cudaMemsetAsync(dst, 0, N * sizeof(T), s->stream));
+            VP_CUDA(s, launch_step_scatter<T>(a, s->ptr<double>(P.L.lost), s->stream));
+        }
+        int nparts = 0;
+        if (P.galerkin) {
+            T *tmp = s->ptr<T>(P.L.tmp);
+            VP_CUDA(s, launch_filter_x<T>(static_cast<const T *>(dst), tmp, P.g.nx, P.g.np, err,
+                                          s->stream));
+            VP_CUDA(s, launch_filter_p<T>(tmp, static_cast<T *>(dst), P.g.nx, P.g.np,
+                                          s->ptr<double>(P.L.piv), s->ptr<double2>(P.L.csx), part,
+                                          P.fel ? 1 : 0, err, s->stream));
+            nparts = filter_p_blocks(P.g.nx, P.g.np);
+        } else if (P.fel) {
+            if (P.kernel == VP_KERNEL_TILED) {
+                nparts = P.ntx * P.ntp;
+            } else {
+                VP_CUDA(s, launch_fel_partials<T>(static_cast<const T *>(dst), P.g.nx, P.g.np,
+                                                  s->ptr<double2>(P.L.csx), part, s->stream));
+                nparts = fel_partial_blocks(P.g.nx, P.g.np);
+            }
+        }
+        if (P.fel) {
+            VP_CUDA(s, launch_fel_finalize(part, nparts, state, s->ptr<double>(P.L.hist), P.hist_cap,
+                                           P.g.dt, 0, s->stream));
+        } else {
+            VP_CUDA(s, launch_count_step(state, P.g.dt, s->stream));
+        }
+        s->cur = 1 - s->cur;
+    }
+    return VP_OK;
+}
+
+vp_status reset_state(vp_sim *s)
+{
+    const Plan &P = s->P;
+    memset(s->host_state, 0, sizeof(s->host_state));
+    s->host_state[ST_A_RE] = s->a0_re;
+    s->host_state[ST_A_IM] = s->a0_im;
+    VP_CUDA(s, cudaMemcpyAsync(s->ws + P.L.state, s->host_state, sizeof(s->host_state),
+                               cudaMemcpyHostToDevice, s->stream));
+    VP_CUDA(s, cudaMemsetAsync(s->ws + P.L.lost, 0, P.nlost * sizeof(double), s->stream));
+    VP_CUDA(s, cudaMemsetAsync(s->ws + P.L.err, 0, sizeof(unsigned), s->stream));
+    VP_CUDA(s, cudaMemsetAsync(s->ws + P.L.hist, 0, (size_t)P.hist_cap * 2 * sizeof(double), s->stream));
+    if (P.fel) {
+        vp_status st = P.precision == VP_FP64 ? fel_bunching<double>(s, s->f(s->cur), 1)
+                                              : fel_bunching<float>(s, s->f(s->cur), 1);
+        if (st != VP_OK) return st;
+    }
+    // the host copy above reads host_state: finish it before the struct is reused
+    VP_CUDA(s, cudaStreamSynchronize(s->stream));
+    return VP_OK;
+}
+
+vp_status check_flags(vp_sim *s)
+{
+    VP_CUDA(s, cudaMemcpyAsync(&s->host_err, s->ws + s->P.L.err, sizeof(unsigned),
+                               cudaMemcpyDeviceToHost, s->stream));
+    VP_CUDA(s, cudaStreamSynchronize(s->stream));
+    if (s->host_err & ERRF_NONFINITE)
+        return fail(s->msg, VP_ERR_NONFINITE, "a step produced a non-finite weight");
+    if (s->host_err & ERRF_TIMEOUT)
+        return fail(s->msg, VP_ERR_TIMEOUT, "a bounded device wait gave up");
+    return VP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *vp_status_string(vp_status st)
+{
+    switch (st) {
+    case VP_OK: return "ok";
+    case VP_ERR_ARG: return "invalid argument";
+    case VP_ERR_CUDA: return "CUDA error";
+    case VP_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case VP_ERR_NONFINITE: return "non-finite weight";
+    case VP_ERR_TIMEOUT: return "device wait timed out";
+    case VP_ERR_STATE: return "call out of order";
+    case VP_ERR_UNSUPPORTED: return "unsupported size or option";
+    }
+    return "unknown status";
+}
+
+vp_status vp_workspace_size(const vp_grid *grid, int32_t basis, const vp_pusher *pusher,
+                            const vp_opts *opts, size_t *bytes)
+{
+    if (!bytes) return VP_ERR_ARG;
+    Plan P;
+    vp_status st = make_plan(grid, basis, pusher, opts, &P, nullptr);
+    if (st != VP_OK) return st;
+    *bytes = P.L.total;
+    return VP_OK;
+}
+
+vp_status vp_create(const vp_grid *grid, int32_t basis, const vp_pusher *pusher,
+                    const vp_opts *opts, void *workspace, size_t workspace_bytes, vp_sim **out)
+{
+    if (!out) return VP_ERR_ARG;
+    *out = nullptr;
+    vp_sim *s = new (std::nothrow) vp_sim();
+    if (!s) return VP_ERR_ARG;
+    vp_status st = make_plan(grid, basis, pusher, opts, &s->P, s->msg);
+    if (st != VP_OK) {
+        delete s;
+        return st;
+    }
+    const Plan &P = s->P;
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0 ||
+        workspace_bytes < P.L.total) {
+        delete s;
+        return VP_ERR_WORKSPACE;
+    }
+    s->ws = static_cast<char *>(workspace);
+    s->stream = static_cast<cudaStream_t>(opts->stream);
+    s->cur = 0;
+    s->f_set = false;
+    s->a0_re = pusher->kind == VP_PUSH_FEL_DKD ? pusher->a0_re : 0.0;
+    s->a0_im = pusher->kind == VP_PUSH_FEL_DKD ? pusher->a0_im : 0.0;
+
+    Geometry &g = s->P.g;
+    auto cleanup = [&](vp_status code) {
+        if (code != VP_OK) delete s;
+        return code;
+    };
+    cudaError_t e = build_tables(g, P.precision, s->ws + P.L.col, s->ws + P.L.row,
+                                 s->ptr<RowBound>(P.L.rowb), s->ptr<double>(P.L.ucol),
+                                 s->ptr<double>(P.L.vcol), s->ptr<double2>(P.L.csx), s->stream);
+    if (e != cudaSuccess) return cleanup(cuda_fail(nullptr, e, "build_tables"));
+    std::vector<double> ucol(g.nx), vcol(g.nx);
+    std::vector<RowBound> rowb(g.np);
+    e = cudaMemcpyAsync(ucol.data(), s->ws + P.L.ucol, g.nx * sizeof(double), cudaMemcpyDeviceToHost,
+                        s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(vcol.data(), s->ws + P.L.vcol, g.nx * sizeof(double),
+                            cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(rowb.data(), s->ws + P.L.rowb, g.np * sizeof(RowBound),
+                            cudaMemcpyDeviceToHost, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cleanup(cuda_fail(nullptr, e, "table readback"));
+
+    g.uc_min = *std::min_element(ucol.begin(), ucol.end());
+    g.uc_max = *std::max_element(ucol.begin(), ucol.end());
+    g.vc_min = *std::min_element(vcol.begin(), vcol.end());
+    g.vc_max = *std::max_element(vcol.begin(), vcol.end());
+    g.vr_min = 1e300;
+    g.vr_max = -1e300;
+    for (const RowBound &b : rowb) {
+        g.vr_min = std::min(g.vr_min, b.v);
+        g.vr_max = std::max(g.vr_max, b.v);
+    }
+    std::vector<double> vcb(2 * P.nblk);
+    for (int b = 0; b < P.nblk; ++b) {
+        double lo = 1e300, hi = -1e300;
+        for (int i = b * kColBlock; i < std::min(g.nx, (b + 1) * kColBlock); ++i) {
+            lo = std::min(lo, vcol[i]);
+            hi = std::max(hi, vcol[i]);
+        }
+        vcb[2 * b] = lo;
+        vcb[2 * b + 1] = hi;
+    }
+    // Thomas pivots of tridiag(1/6, 2/3, 1/6) from the first row, and their limits
+    std::vector<double> piv(2 * kPivots + 2);
+    double cprev = 0.0;
+    for (int r = 0; r < kPivots; ++r) {
+        const double beta = 2.0 / 3.0 - (r == 0 ? 0.0 : cprev / 6.0);
+        piv[2 * r] = (1.0 / 6.0) / beta;
+        piv[2 * r + 1] = 1.0 / beta;
+        cprev = piv[2 * r];
+    }
+    const double beta_inf = 1.0 / 3.0 + 1.0 / (2.0 * sqrt(3.0));
+    piv[2 * kPivots] = (1.0 / 6.0) / beta_inf;
+    piv[2 * kPivots + 1] = 1.0 / beta_inf;
+    e = cudaMemcpyAsync(s->ws + P.L.vcb, vcb.data(), vcb.size() * sizeof(double),
+                        cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->ws + P.L.piv, piv.data(), piv.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->ws + P.L.err, 0, sizeof(unsigned), s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cleanup(cuda_fail(nullptr, e, "table upload"));
+    *out = s;
+    return VP_OK;
+}
+
+static vp_status set_f_common(vp_sim *s, const void *src, int32_t dtype, size_t n, bool device)
+{
+    if (!s) return VP_ERR_ARG;
+    const Plan &P = s->P;
+    const size_t N = (size_t)P.g.nx * P.g.np;
+    if (!src || n != N || (dtype != VP_FP32 && dtype != VP_FP64))
+        return fail(s->msg, VP_ERR_ARG, "set_f: need %zu values of dtype FP32/FP64", N);
+    s->cur = 0;
+    void *dst = s->f(0);
+    const size_t szs = P.precision == VP_FP64 ? 8 : 4;
+    if (dtype == P.precision) {
+        VP_CUDA(s, cudaMemcpyAsync(dst, src, N * szs,
+                                   device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                   s->stream));
+    } else if (device) {
+        if (dtype == VP_FP64)
+            VP_CUDA(s, launch_convert<double, float>(static_cast<const double *>(src),
+                                                     static_cast<float *>(dst), N, s->stream));
+        else
+            VP_CUDA(s, launch_convert<float, double>(static_cast<const float *>(src),
+                                                     static_cast<double *>(dst), N, s->stream));
+    } else {
+        std::vector<char> tmp(N * szs);
+        if (dtype == VP_FP64) {
+            const double *in = static_cast<const double *>(src);
+            float *o = reinterpret_cast<float *>(tmp.data());
+            for (size_t k = 0; k < N; ++k) o[k] = (float)in[k];
+        } else {
+            const float *in = static_cast<const float *>(src);
+            double *o = reinterpret_cast<double *>(tmp.data());
+            for (size_t k = 0; k < N; ++k) o[k] = (double)in[k];
+        }
+        VP_CUDA(s, cudaMemcpyAsync(dst, tmp.data(), N * szs, cudaMemcpyHostToDevice, s->stream));
+        VP_CUDA(s, cudaStreamSynchronize(s->stream));
+    }
+    s->f_set = true;
+    return reset_state(s);
+}
+
+vp_status vp_set_f(vp_sim *s, const void *host, int32_t dtype, size_t n)
+{
+    return set_f_common(s, host, dtype, n, false);
+}
+
+vp_status vp_set_f_device(vp_sim *s, const void *dev, int32_t dtype, size_t n)
+{
+    return set_f_common(s, dev, dtype, n, true);
+}
+
+vp_status vp_step(vp_sim *s, int32_t n)
+{
+    if (!s) return VP_ERR_ARG;
+    if (n < 0) return fail(s->msg, VP_ERR_ARG, "negative step count");
+    if (!s->f_set) return fail(s->msg, VP_ERR_STATE, "vp_step before vp_set_f");
+    return s->P.precision == VP_FP64 ? do_steps<double>(s, n) : do_steps<float>(s, n);
+}
+
+static vp_status get_f_common(vp_sim *s, void *dstp, int32_t dtype, size_t n, bool device)
+{
+    if (!s) return VP_ERR_ARG;
+    const Plan &P = s->P;
+    const size_t N = (size_t)P.g.nx * P.g.np;
+    if (!dstp || n != N || (dtype != VP_FP32 && dtype != VP_FP64))
+        return fail(s->msg, VP_ERR_ARG, "get_f: need room for %zu values of dtype FP32/FP64", N);
+    if (!s->f_set) return fail(s->msg, VP_ERR_STATE, "vp_get_f before vp_set_f");
+    const void *src = s->f(s->cur);
+    const size_t szs = P.precision == VP_FP64 ? 8 : 4;
+    if (dtype == P.precision) {
+        VP_CUDA(s, cudaMemcpyAsync(dstp, src, N * szs,
+                                   device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                   s->stream));
+    } else if (device) {
+        if (P.precision == VP_FP32)
+            VP_CUDA(s, launch_convert<float, double>(static_cast<const float *>(src),
+                                                     static_cast<double *>(dstp), N, s->stream));
+        else
+            VP_CUDA(s, launch_convert<double, float>(static_cast<const double *>(src),
+                                                     static_cast<float *>(dstp), N, s->stream));
+    } else {
+        std::vector<char> tmp(N * szs);
+        VP_CUDA(s, cudaMemcpyAsync(tmp.data(), src, N * szs, cudaMemcpyDeviceToHost, s->stream));
+        VP_CUDA(s, cudaStreamSynchronize(s->stream));
+        if (P.precision == VP_FP32) {
+            const float *in = reinterpret_cast<const float *>(tmp.data());
+            double *o = static_cast<double *>(dstp);
+            for (size_t k = 0; k < N; ++k) o[k] = in[k];
+        } else {
+            const double *in = reinterpret_cast<const double *>(tmp.data());
+            float *o = static_cast<float *>(dstp);
+            for (size_t k = 0; k < N; ++k) o[k] = (float)in[k];
+        }
+    }
+    if (device) return VP_OK;
+    return check_flags(s);
+}
+
+vp_status vp_get_f(vp_sim *s, void *host, int32_t dtype, size_t n)
+{
+    return get_f_common(s, host, dtype, n, false);
+}
+
+vp_status vp_get_f_device(vp_sim *s, void *dev, int32_t dtype, size_t n)
+{
+    return get_f_common(s, dev, dtype, n, true);
+}
+
+vp_status vp_moments(vp_sim *s, vp_moments_t *out)
+{
+    if (!s || !out) return VP_ERR_ARG;
+    if (!s->f_set) return fail(s->msg, VP_ERR_STATE, "vp_moments before vp_set_f");
+    const Plan &P = s->P;
+    double *mpart = s->ptr<double>(P.L.mpart);
+    double *mout = s->ptr<double>(P.L.mout);
+    if (P.precision == VP_FP64)
+        VP_CUDA(s, launch_moments<double>(static_cast<const double *>(s->f(s->cur)), P.g,
+                                          s->ptr<double2>(P.L.csx), mpart, P.nmblk, s->stream));
+    else
+        VP_CUDA(s, launch_moments<float>(static_cast<const float *>(s->f(s->cur)), P.g,
+                                         s->ptr<double2>(P.L.csx), mpart, P.nmblk, s->stream));
+    VP_CUDA(s, launch_moments_finalize(mpart, P.nmblk, s->ptr<double>(P.L.lost), P.nlost, mout,
+                                       s->stream));
+    VP_CUDA(s, cudaMemcpyAsync(s->host_mout, mout, kMoutLen * sizeof(double), cudaMemcpyDeviceToHost,
+                               s->stream));
+    VP_CUDA(s, cudaMemcpyAsync(s->host_state, s->ws + P.L.state, sizeof(s->host_state),
+                               cudaMemcpyDeviceToHost, s->stream));
+    vp_status st = check_flags(s);
+    const double *m = s->host_mout;
+    const double hh = P.g.hx * P.g.hp;
+    const double S = m[0];
+    memset(out, 0, sizeof(*out));
+    out->sum_w = S;
+    out->mass = S * hh;
+    out->mean_x = m[1] / S;
+    out->mean_p = m[2] / S;
+    out->var_x = m[3] / S - out->mean_x * out->mean_x;
+    out->var_p = m[4] / S - out->mean_p * out->mean_p;
+    out->cov_xp = m[5] / S - out->mean_x * out->mean_p;
+    out->a_re = s->host_state[ST_A_RE];
+    out->a_im = s->host_state[ST_A_IM];
+    out->energy = P.fel ? out->mean_p + out->a_re * out->a_re + out->a_im * out->a_im : m[6] / S;
+    out->trapped = m[7] * hh;
+    out->entropy = m[8] * hh;
+    out->neg_mass = m[9] * hh;
+    out->b_re = m[10] / S;
+    out->b_im = -m[11] / S;
+    out->max_abs_w = m[12];
+    out->lost_mass = m[kNumMoments] * hh;
+    out->tau = s->host_state[ST_TAU];
+    out->step = (int64_t)s->host_state[ST_STEP];
+    return st;
+}
+
+vp_status vp_field_history(vp_sim *s, double *re_im, size_t max_entries, size_t *count)
+{
+    if (!s || !count || (!re_im && max_entries)) return VP_ERR_ARG;
+    const Plan &P = s->P;
+    std::vector<double> h((size_t)P.hist_cap * 2);
+    VP_CUDA(s, cudaMemcpyAsync(h.data(), s->ws + P.L.hist, h.size() * sizeof(double),
+                               cudaMemcpyDeviceToHost, s->stream));
+    VP_CUDA(s, cudaMemcpyAsync(s->host_state, s->ws + P.L.state, sizeof(s->host_state),
+                               cudaMemcpyDeviceToHost, s->stream));
+    VP_CUDA(s, cudaStreamSynchronize(s->stream));
+    const long step = (long)s->host_state[ST_STEP];
+    size_t c = (size_t)std::min<long>(step, P.hist_cap);
+    c = std::min(c, max_entries);
+    for (size_t k = 0; k < c; ++k) {
+        const long st = step - (long)c + (long)k;
+        const long slot = st % P.hist_cap;
+        re_im[2 * k] = h[2 * slot];
+        re_im[2 * k + 1] = h[2 * slot + 1];
+    }
+    *count = P.fel ? c : 0;
+    return VP_OK;
+}
+
+vp_status vp_sync(vp_sim *s)
+{
+    if (!s) return VP_ERR_ARG;
+    return check_flags(s);
+}
+
+vp_status vp_set_stream(vp_sim *s, void *stream)
+{
+    if (!s) return VP_ERR_ARG;
+    s->stream = static_cast<cudaStream_t>(stream);
+    return VP_OK;
+}
+
+vp_status vp_state_device(vp_sim *s, void **dev)
+{
+    if (!s || !dev) return VP_ERR_ARG;
+    *dev = s->f(s->cur);
+    return VP_OK;
+}
+
+void vp_destroy(vp_sim *s) { delete s; }
+
+const char *vp_last_error(const vp_sim *s) { return s ? s->msg : "NULL simulation"; }
+
+}  // extern "C"

@@ -1,0 +1,246 @@
+// vp_filter.cu -- the mass-matrix solve Lambda w_fin = r (Sec. III update equation)
+// for the tent basis, Lambda = (hx Tx) (x) (hp Tp), T = tridiag(1/6, 2/3, 1/6).
+// The deposit omits the common factor hx hp, so here T w = r is solved per axis.
+//
+// x (periodic): T is cyclic. With z = sqrt(3) - 2 the root of z^2 + 4z + 1 = 0,
+//   T = -(1 / (6 z)) (1 - z S)(1 - z S^{-1})   (S the cyclic shift),
+// so T^{-1} r is a causal recursion y_i = r_i + z y_{i-1}, an anticausal one
+// u_i = y_i + z u_{i+1}, and the factor -6z. Each thread runs the recursions
+// over one chunk of a row held in shared memory; the value entering a chunk is
+// the exact cyclic sum (1/(1 - z^nx)) sum_k z^k r_{i-k}, truncated after K
+// terms where z^K is below the precision's round-off.
+//
+// p (open): T is the np x np Toeplitz block; the Thomas algorithm solves it.
+// Its pivots depend only on the distance from the first row and reach their
+// limit to FP64 precision within kPivots rows, so they come from a small
+// table. A chunk of rows [s, e) starts the forward sweep K rows early (or at
+// row 0) and the back substitution K rows late (or at row np-1); the error of
+// the truncation is |z|^K.
+#include <math.h>
+
+#include "vp_internal.h"
+
+namespace vp {
+namespace {
+
+constexpr double kZ = -0.26794919243112270647255365849413;   // sqrt(3) - 2
+
+template <typename T>
+struct Trunc;
+template <>
+struct Trunc<float> {
+    static constexpr int K = 16;   // |z|^16 = 7e-10
+};
+template <>
+struct Trunc<double> {
+    static constexpr int K = 32;   // |z|^32 = 5e-19
+};
+
+__device__ __forceinline__ int padx(int i) { return i + (i >> 5); }
+
+template <typename T>
+__global__ void filter_x_kernel(const T *__restrict__ in, T *__restrict__ out, int nx, int np,
+                                unsigned *err)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *buf = reinterpret_cast<T *>(smem_raw);
+    const int j = blockIdx.x;
+    const T *src = in + (size_t)j * nx;
+    T *dst = out + (size_t)j * nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) buf[padx(i)] = src[i];
+    __syncthreads();
+
+    const T z = (T)kZ;
+    const int K = Trunc<T>::K;
+    const int L = nx < K ? nx : K;
+    const T cyc = (T)(1.0 / (1.0 - pow(kZ, (double)nx)));
+    const int C = (nx + blockDim.x - 1) / blockDim.x;
+    const int s = threadIdx.x * C;
+    const int e = min(s + C, nx);
+    const bool active = s < nx;
+
+    // causal: value y_{s-1}
+    T init = T(0);
+    if (active) {
+        T zk = T(1);
+        int idx = s - 1;
+        if (idx < 0) idx += nx;
+        for (int k = 0; k < L; ++k) {
+            init += zk * buf[padx(idx)];
+            zk *= z;
+            if (--idx < 0) idx += nx;
+        }
+        init *= cyc;
+    }
+    __syncthreads();
+    if (active) {
+        T y = init;
+        for (int i = s; i < e; ++i) {
+            y = buf[padx(i)] + z * y;
+            buf[padx(i)] = y;
+        }
+    }
+    __syncthreads();
+    // anticausal: value u_e
+    if (active) {
+        T zk = T(1);
+        int idx = e;
+        if (idx >= nx) idx -= nx;
+        init = T(0);
+        for (int k = 0; k < L; ++k) {
+            init += zk * buf[padx(idx)];
+            zk *= z;
+            if (++idx >= nx) idx -= nx;
+        }
+        init *= cyc;
+    }
+    __syncthreads();
+    const T scale = (T)(-6.0 * kZ);
+    if (active) {
+        T u = init;
+        for (int i = e - 1; i >= s; --i) {
+            u = buf[padx(i)] + z * u;
+            buf[padx(i)] = u * scale;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) dst[i] = buf[padx(i)];
+    (void)np;
+    (void)err;
+}
+
+constexpr int kPCols = 32;    // columns per warp
+constexpr int kPWarps = 4;    // warps per block (adjacent column groups)
+constexpr int kPChunk = 128;  // rows per chunk
+
+template <typename T>
+__device__ __forceinline__ void kahan_add(T &sum, T &comp, T v)
+{
+    const T y = v - comp;
+    const T t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+// piv[2 r] = c'_r (super-diagonal factor), piv[2 r + 1] = 1 / beta_r, r < kPivots;
+// piv[2 kPivots], piv[2 kPivots + 1] = their limits.
+template <typename T>
+__global__ void __launch_bounds__(kPCols *kPWarps)
+    filter_p_kernel(const T *__restrict__ in, T *__restrict__ out, int nx, int np,
+                    const double *__restrict__ piv, const double2 *__restrict__ csx,
+                    double *part, int want_part, unsigned *err)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *gbuf = reinterpret_cast<T *>(smem_raw);   // [(kPChunk + K) rows][kPCols * kPWarps]
+    __shared__ double s_red[3][kPWarps];
+    const int K = Trunc<T>::K;
+    const int W = kPCols * kPWarps;
+    const int lane = threadIdx.x, wy = threadIdx.y;
+    const int tid = wy * kPCols + lane;
+    const int col = blockIdx.x * W + tid;
+    const bool valid = col < nx;
+    const int s = blockIdx.y * kPChunk;
+    const int e = min(s + kPChunk, np);
+    const int fe = min(e + K, np);          // forward sweep end (exclusive)
+    const int fs = max(s - K, 0);           // forward sweep start
+    const T sixth = (T)(1.0 / 6.0);
+    const T cp_inf = (T)piv[2 * kPivots], ib_inf = (T)piv[2 * kPivots + 1];
+
+    T g = T(0);
+    if (valid) {
+        for (int r = fs; r < fe; ++r) {
+            const T ib = r < kPivots ? (T)piv[2 * r + 1] : ib_inf;
+            const T rv = in[(size_t)r * nx + col];
+            g = (rv - sixth * g) * ib;
+            if (r >= s) gbuf[(size_t)(r - s) * W + tid] = g;
+        }
+    }
+    // back substitution from fe - 1 (exact at the last row: w_{np-1} = g_{np-1})
+    T wsum = T(0), wcomp = T(0);
+    bool bad = false;
+    if (valid) {
+        T w = T(0);
+        for (int r = fe - 1; r >= s; --r) {
+            const T cp = r < kPivots ? (T)piv[2 * r] : cp_inf;
+            const T gv = gbuf[(size_t)(r - s) * W + tid];
+            w = (r == np - 1) ? gv : gv - cp * w;
+            if (r < e) {
+                out[(size_t)r * nx + col] = w;
+                bad |= !isfinite(w);
+                if (want_part) kahan_add(wsum, wcomp, w);
+            }
+        }
+    }
+    if (bad) atomicOr(err, ERRF_NONFINITE);
+    if (!want_part) return;
+    double pw = 0.0, pc = 0.0, ps = 0.0;
+    if (valid) {
+        pw = (double)wsum - (double)wcomp;
+        const double2 t = csx[col];
+        pc = pw * t.x;
+        ps = pw * t.y;
+    }
+    double v[3] = {pw, pc, ps};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+        if (lane == 0) s_red[q][wy] = v[q];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+        for (int q = 0; q < 3; ++q) {
+            double t = 0.0;
+            for (int w = 0; w < kPWarps; ++w) t += s_red[q][w];
+            part[3 * b + q] = t;
+        }
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_filter_x(const T *in, T *out, int nx, int np, unsigned *err, cudaStream_t s)
+{
+    const size_t smem = (size_t)(nx + nx / 32 + 1) * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(filter_x_kernel<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    filter_x_kernel<T><<<np, 256, smem, s>>>(in, out, nx, np, err);
+    return cudaGetLastError();
+}
+
+int filter_p_blocks(int nx, int np)
+{
+    const int W = kPCols * kPWarps;
+    return ((nx + W - 1) / W) * ((np + kPChunk - 1) / kPChunk);
+}
+
+template <typename T>
+cudaError_t launch_filter_p(const T *in, T *out, int nx, int np, const double *piv,
+                            const double2 *csx, double *part, int want_part, unsigned *err,
+                            cudaStream_t s)
+{
+    const int W = kPCols * kPWarps;
+    const size_t smem = (size_t)(kPChunk + Trunc<T>::K) * W * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(filter_p_kernel<T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((nx + W - 1) / W, (np + kPChunk - 1) / kPChunk);
+    dim3 block(kPCols, kPWarps);
+    filter_p_kernel<T><<<grid, block, smem, s>>>(in, out, nx, np, piv, csx, part, want_part, err);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_filter_x<float>(const float *, float *, int, int, unsigned *,
+                                            cudaStream_t);
+template cudaError_t launch_filter_x<double>(const double *, double *, int, int, unsigned *,
+                                             cudaStream_t);
+template cudaError_t launch_filter_p<float>(const float *, float *, int, int, const double *,
+                                            const double2 *, double *, int, unsigned *,
+                                            cudaStream_t);
+template cudaError_t launch_filter_p<double>(const double *, double *, int, int, const double *,
+                                             const double2 *, double *, int, unsigned *,
+                                             cudaStream_t);
+
+}  // namespace vp

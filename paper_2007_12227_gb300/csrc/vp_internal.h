@@ -1,0 +1,124 @@
+// vp_internal.h -- device data layout and launch entry points shared by the
+// translation units of libvlasov (not part of the public C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vlasov.h"
+
+namespace vp {
+
+// ---------------------------------------------------------------------------
+// Push in displacement form (Sec. II flow of one mesh node over the step h).
+//
+// Every pusher of this library moves node (i, j) by
+//   du = (C.ui + R.ui) + (C.uf + R.uf) + KU * s        [cells along x]
+//   dv = (C.vi + R.vi) + (C.vf + R.vf) + KV * s        [cells along p]
+//   s  = alpha * sin(a_i + y_j) + beta * cos(a_i + y_j)
+// with per-column entries C (index i) and per-row entries R (index j) built
+// once in FP64 on the device, integer parts split off so that the FP32 path
+// keeps sub-cell precision, and (alpha, beta) fixed per sim or, for the FEL,
+// read from the field A^{n+1/2} every step. sin/cos of the sum come from the
+// angle-addition identity of the tabulated sin/cos of a_i and y_j.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct ColEntry {
+    int ui, vi;
+    T uf, vf, sa, ca;
+};
+
+template <typename T>
+struct RowEntry {
+    int ui, vi;
+    T uf, vf, sy, cy;
+};
+
+// FP64 per-row values used only to bound the source window of a tile.
+struct RowBound {
+    double u, v, y;
+    double pad;
+};
+
+// Device FEL / step state (doubles).
+enum {
+    ST_A_RE = 0, ST_A_IM, ST_B_RE, ST_B_IM, ST_AH_RE, ST_AH_IM, ST_TAU, ST_STEP,
+    ST_HIST_HEAD, ST_NSTATE = 16
+};
+
+// Device error flag bits.
+enum { ERRF_NONFINITE = 1u, ERRF_TIMEOUT = 2u, ERRF_WINDOW = 4u };
+
+constexpr int kColBlock = 32;     // column block of the V-bound table
+constexpr int kNumMoments = 13;   // accumulators of the moments reduction (lost follows)
+
+struct Geometry {
+    int nx, np;
+    double x0, x1, p0, p1, hx, hp;
+    int basis, kind, potential, projection;
+    double v_sign, omega, dt;
+    double KU, KV;          // coefficients of the sine term
+    double alpha0, beta0;   // sine-term weights for non-FEL pushers
+    double a_pad;           // bound on |a_i - x_i|
+    double uc_min, uc_max;  // bounds of the column part of du
+    double vc_min, vc_max;  // bounds of the column part of dv
+    double vr_min, vr_max;  // bounds of the row part of dv
+};
+
+template <typename T>
+struct StepArgs {
+    const T *src;
+    T *dst;
+    const ColEntry<T> *col;
+    const RowEntry<T> *row;
+    const RowBound *rowb;
+    const double *vcb;      // per 32-column block: min, max of the column part of dv
+    const double *state;    // ST_* (FEL reads A^{n+1/2})
+    const double2 *csx;     // (cos x_i, sin x_i) in FP64, for the FEL partial sums
+    double *tile_lost;      // per tile, cumulative lost weight
+    double *tile_part;      // per tile: sum w, sum w cos x, sum w sin x (FEL)
+    unsigned *err;
+    Geometry g;
+    int tx, tp, ntx, ntp;   // tile shape and counts
+    int fel_partials;       // emit FEL partials from the step kernel
+};
+
+// ---- launch entry points (defined in the .cu files) -----------------------
+cudaError_t build_tables(const Geometry &g, int precision, void *col, void *row,
+                         RowBound *rowb, double *ucol, double *vcol, double2 *csx, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_step_tiled(const StepArgs<T> &a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_step_scatter(const StepArgs<T> &a, double *lost_acc, cudaStream_t s);
+template <typename T>
+size_t tiled_smem_bytes(int tx, int tp);
+
+template <typename T>
+cudaError_t launch_filter_x(const T *in, T *out, int nx, int np, unsigned *err, cudaStream_t s);
+template <typename T>
+cudaError_t launch_filter_p(const T *in, T *out, int nx, int np, const double *piv,
+                            const double2 *csx, double *part, int want_part, unsigned *err,
+                            cudaStream_t s);
+constexpr int kPivots = 64;       // exact Thomas pivots kept for the first rows
+int filter_p_blocks(int nx, int np);
+
+template <typename T>
+cudaError_t launch_fel_partials(const T *w, int nx, int np, const double2 *csx, double *part,
+                                cudaStream_t s);
+int fel_partial_blocks(int nx, int np);
+cudaError_t launch_fel_finalize(const double *part, int nparts, double *state, double *hist,
+                                int hist_cap, double dt, int init, cudaStream_t s);
+cudaError_t launch_count_step(double *state, double dt, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_moments(const T *w, const Geometry &g, const double2 *csx, double *part,
+                           int nblocks, cudaStream_t s);
+int moment_blocks(int nx, int np);
+cudaError_t launch_moments_finalize(const double *part, int nblocks, const double *lost,
+                                    int nlost, double *out, cudaStream_t s);
+
+template <typename Tin, typename Tout>
+cudaError_t launch_convert(const Tin *in, Tout *out, size_t n, cudaStream_t s);
+
+}  // namespace vp

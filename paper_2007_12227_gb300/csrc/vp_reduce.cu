@@ -1,0 +1,283 @@
+// vp_reduce.cu -- FP64 reductions over the weights.
+//
+// FEL field (Sec. IV.B, dA/dz = <exp(-i Phi)>, detuning and space charge zero),
+// drift-kick-drift in time:
+//   A^{n+1/2} = A^n + h/2 b^n,  push with A^{n+1/2},  b^{n+1} = <exp(-i theta)>
+//   of the new weights,  A^{n+1} = A^{n+1/2} + h/2 b^{n+1}.
+// The bunching comes from per-block partial sums (sum w, sum w cos theta,
+// sum w sin theta), reduced here in a fixed order so that results do not
+// depend on scheduling.
+//
+// Moments (Sec. IV diagnostics: sum of weights, entropy): FP64 accumulation per
+// thread, per-block partials, fixed-order final sum.
+#include <math.h>
+
+#include "vp_internal.h"
+
+namespace vp {
+namespace {
+
+constexpr int kRedThreads = 256;
+
+template <typename T>
+__device__ __forceinline__ void kahan_add(T &sum, T &comp, T v)
+{
+    const T y = v - comp;
+    const T t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+// one block per 32-column strip x row chunk: column sums (compensated) then x cos/sin
+constexpr int kFelRows = 256;
+
+template <typename T>
+__global__ void fel_partials_kernel(const T *__restrict__ w, int nx, int np,
+                                    const double2 *__restrict__ csx, double *part)
+{
+    __shared__ double s_red[3][kRedThreads / 32];
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const int col = blockIdx.x * 32 + lane;
+    const int r0 = blockIdx.y * kFelRows;
+    const int r1 = min(r0 + kFelRows, np);
+    T s = T(0), c = T(0);
+    if (col < nx)
+        for (int r = r0 + wy; r < r1; r += kRedThreads / 32) kahan_add(s, c, w[(size_t)r * nx + col]);
+    double pw = (double)s - (double)c, pc = 0.0, ps = 0.0;
+    if (col < nx) {
+        const double2 t = csx[col];
+        pc = pw * t.x;
+        ps = pw * t.y;
+    }
+    double v[3] = {pw, pc, ps};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_down_sync(0xffffffffu, v[q], o);
+        if (lane == 0) s_red[q][wy] = v[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+        for (int q = 0; q < 3; ++q) {
+            double t = 0.0;
+            for (int k = 0; k < kRedThreads / 32; ++k) t += s_red[q][k];
+            part[3 * b + q] = t;
+        }
+    }
+}
+
+__global__ void fel_finalize_kernel(const double *__restrict__ part, int nparts, double *state,
+                                    double *hist, int hist_cap, double dt, int init)
+{
+    __shared__ double s[3][kRedThreads];
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int k = threadIdx.x; k < nparts; k += blockDim.x) {
+        a0 += part[3 * k];
+        a1 += part[3 * k + 1];
+        a2 += part[3 * k + 2];
+    }
+    s[0][threadIdx.x] = a0;
+    s[1][threadIdx.x] = a1;
+    s[2][threadIdx.x] = a2;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int q = 0; q < 3; ++q) s[q][threadIdx.x] += s[q][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const double sw = s[0][0];
+    const double b_re = s[1][0] / sw, b_im = -s[2][0] / sw;
+    state[ST_B_RE] = b_re;
+    state[ST_B_IM] = b_im;
+    if (init) {
+        // A^0 already stored; A^{1/2} = A^0 + h/2 b^0
+        state[ST_AH_RE] = state[ST_A_RE] + 0.5 * dt * b_re;
+        state[ST_AH_IM] = state[ST_A_IM] + 0.5 * dt * b_im;
+        return;
+    }
+    const double are = state[ST_AH_RE] + 0.5 * dt * b_re;
+    const double aim = state[ST_AH_IM] + 0.5 * dt * b_im;
+    state[ST_A_RE] = are;
+    state[ST_A_IM] = aim;
+    state[ST_AH_RE] = are + 0.5 * dt * b_re;
+    state[ST_AH_IM] = aim + 0.5 * dt * b_im;
+    const long step = (long)state[ST_STEP];
+    if (hist && hist_cap > 0) {
+        const long slot = step % hist_cap;
+        hist[2 * slot] = are;
+        hist[2 * slot + 1] = aim;
+    }
+    state[ST_STEP] = (double)(step + 1);
+    state[ST_TAU] = (double)(step + 1) * dt;
+}
+
+// plain step counter for non-FEL sims
+__global__ void count_step_kernel(double *state, double dt)
+{
+    const double st = state[ST_STEP] + 1.0;
+    state[ST_STEP] = st;
+    state[ST_TAU] = st * dt;
+}
+
+template <typename T>
+__device__ __forceinline__ double wlogw(T w)
+{
+    return (double)(w * log(w));
+}
+
+template <typename T>
+__global__ void moments_kernel(const T *__restrict__ w, Geometry g, const double2 *__restrict__ csx,
+                               double *part)
+{
+    __shared__ double s_red[kNumMoments][kRedThreads / 32];
+    double acc[kNumMoments];
+#pragma unroll
+    for (int q = 0; q < kNumMoments; ++q) acc[q] = 0.0;
+    const size_t n = (size_t)g.nx * g.np;
+    const double hsep = fabs(g.v_sign);
+    const bool pend = (g.kind == VP_PUSH_LEAPFROG_KDK && g.potential == VP_POT_PENDULUM);
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const T wt = w[idx];
+        if (wt == T(0)) continue;
+        const int j = (int)(idx / g.nx), i = (int)(idx - (size_t)j * g.nx);
+        const double x = g.x0 + i * g.hx, p = g.p0 + j * g.hp;
+        const double ww = (double)wt;
+        const double2 cs = csx[i];
+        double V = 0.0;
+        if (g.potential == VP_POT_PENDULUM) V = -g.v_sign * cs.x;
+        else if (g.potential == VP_POT_HARMONIC) V = 0.5 * g.omega * g.omega * x * x;
+        const double H = 0.5 * p * p + V;
+        acc[0] += ww;
+        acc[1] += ww * x;
+        acc[2] += ww * p;
+        acc[3] += ww * x * x;
+        acc[4] += ww * p * p;
+        acc[5] += ww * x * p;
+        acc[6] += ww * H;
+        if (pend && H < hsep) acc[7] += ww;
+        if (wt > T(0)) acc[8] -= wlogw(wt);
+        else acc[9] += ww;
+        acc[10] += ww * cs.x;
+        acc[11] += ww * cs.y;
+        acc[12] = fmax(acc[12], fabs(ww));
+    }
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < kNumMoments; ++q) {
+        double v = acc[q];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double u = __shfl_down_sync(0xffffffffu, v, o);
+            v = (q == 12) ? fmax(v, u) : v + u;
+        }
+        if (lane == 0) s_red[q][wy] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < kNumMoments) {
+        const int q = threadIdx.x;
+        double t = 0.0;
+        for (int k = 0; k < kRedThreads / 32; ++k) t = (q == 12) ? fmax(t, s_red[q][k]) : t + s_red[q][k];
+        part[(size_t)blockIdx.x * kNumMoments + q] = t;
+    }
+}
+
+__global__ void moments_finalize_kernel(const double *__restrict__ part, int nblocks,
+                                        const double *__restrict__ lost, int nlost, double *out)
+{
+    const int q = threadIdx.x;
+    if (q < kNumMoments) {
+        double t = 0.0;
+        for (int b = 0; b < nblocks; ++b) {
+            const double v = part[(size_t)b * kNumMoments + q];
+            t = (q == 12) ? fmax(t, v) : t + v;
+        }
+        out[q] = t;
+    } else if (q == kNumMoments) {
+        double t = 0.0;
+        for (int b = 0; b < nlost; ++b) t += lost[b];
+        out[q] = t;
+    }
+}
+
+template <typename Tin, typename Tout>
+__global__ void convert_kernel(const Tin *__restrict__ in, Tout *__restrict__ out, size_t n)
+{
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (size_t)gridDim.x * blockDim.x)
+        out[k] = (Tout)in[k];
+}
+
+}  // namespace
+
+int fel_partial_blocks(int nx, int np)
+{
+    return ((nx + 31) / 32) * ((np + kFelRows - 1) / kFelRows);
+}
+
+template <typename T>
+cudaError_t launch_fel_partials(const T *w, int nx, int np, const double2 *csx, double *part,
+                                cudaStream_t s)
+{
+    dim3 grid((nx + 31) / 32, (np + kFelRows - 1) / kFelRows);
+    fel_partials_kernel<T><<<grid, kRedThreads, 0, s>>>(w, nx, np, csx, part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fel_finalize(const double *part, int nparts, double *state, double *hist,
+                                int hist_cap, double dt, int init, cudaStream_t s)
+{
+    fel_finalize_kernel<<<1, kRedThreads, 0, s>>>(part, nparts, state, hist, hist_cap, dt, init);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_count_step(double *state, double dt, cudaStream_t s)
+{
+    count_step_kernel<<<1, 1, 0, s>>>(state, dt);
+    return cudaGetLastError();
+}
+
+int moment_blocks(int nx, int np)
+{
+    const size_t n = (size_t)nx * np;
+    size_t b = (n + kRedThreads - 1) / kRedThreads;
+    if (b > 152 * 8) b = 152 * 8;
+    return (int)b;
+}
+
+template <typename T>
+cudaError_t launch_moments(const T *w, const Geometry &g, const double2 *csx, double *part,
+                           int nblocks, cudaStream_t s)
+{
+    moments_kernel<T><<<nblocks, kRedThreads, 0, s>>>(w, g, csx, part);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_moments_finalize(const double *part, int nblocks, const double *lost, int nlost,
+                                    double *out, cudaStream_t s)
+{
+    moments_finalize_kernel<<<1, 32, 0, s>>>(part, nblocks, lost, nlost, out);
+    return cudaGetLastError();
+}
+
+template <typename Tin, typename Tout>
+cudaError_t launch_convert(const Tin *in, Tout *out, size_t n, cudaStream_t s)
+{
+    size_t b = (n + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    convert_kernel<Tin, Tout><<<(int)b, 256, 0, s>>>(in, out, n);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_fel_partials<float>(const float *, int, int, const double2 *, double *,
+                                                cudaStream_t);
+template cudaError_t launch_fel_partials<double>(const double *, int, int, const double2 *,
+                                                 double *, cudaStream_t);
+template cudaError_t launch_moments<float>(const float *, const Geometry &, const double2 *,
+                                           double *, int, cudaStream_t);
+template cudaError_t launch_moments<double>(const double *, const Geometry &, const double2 *,
+                                            double *, int, cudaStream_t);
+template cudaError_t launch_convert<float, double>(const float *, double *, size_t, cudaStream_t);
+template cudaError_t launch_convert<double, float>(const double *, float *, size_t, cudaStream_t);
+
+}  // namespace vp

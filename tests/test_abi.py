@@ -1,0 +1,124 @@
+"""The C-ABI library builds, loads and exports every symbol include/vlasov.h declares.
+
+No CUDA device is needed: only host-side entry points (workspace sizing and
+argument checks) are called.
+"""
+import ctypes as C
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+import __graft_entry__  # noqa: F401  (puts the repo root on sys.path)
+from paper_2007_12227_gb300 import build as B
+from paper_2007_12227_gb300 import inputs as I
+from paper_2007_12227_gb300 import vlasov as V
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "vlasov.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return V.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(vp_[a-z_]+)\s*\(", text)))
+
+
+def test_every_declared_function_is_exported_and_bound(lib):
+    names = declared_functions()
+    assert len(names) >= 14
+    bound = {n for n, _, _ in V._SIGNATURES}
+    for n in names:
+        assert hasattr(lib, n), f"{n} not exported"
+        assert n in bound, f"{n} has no binding"
+    out = subprocess.run(["nm", "-D", "--defined-only", V.LIB_PATH], capture_output=True, text=True)
+    if out.returncode == 0:
+        exported = set(re.findall(r"\bT (vp_[a-z_]+)\b", out.stdout))
+        assert set(names) <= exported
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    src = tmp_path / "sz.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "vlasov.h"\n'
+                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(vp_grid), '
+                   'sizeof(vp_pusher), sizeof(vp_opts), sizeof(vp_moments_t), '
+                   'offsetof(vp_moments_t, step)); return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    want = [C.sizeof(V.vp_grid), C.sizeof(V.vp_pusher), C.sizeof(V.vp_opts),
+            C.sizeof(V.vp_moments_t), V.vp_moments_t.step.offset]
+    assert got == want
+
+
+def _cfg(nx=128, np_=96, basis=V.VP_BASIS_CUBIC_BSPLINE, precision=V.VP_FP32, kind=0, pot=1):
+    g = V.vp_grid(nx, np_, -3.141592653589793, 3.141592653589793, -3.0, 3.0)
+    pu = V.vp_pusher(kind, pot, 1.0, 1.0, 0.05, 0.0, 0.0)
+    o = V.vp_opts(precision, 0, 0, 0, 0, 0, None)
+    return g, basis, pu, o
+
+
+def test_workspace_size_scales_with_grid_and_precision(lib):
+    g, b, pu, o = _cfg()
+    n32 = V.vp_workspace_size(g, b, pu, o)
+    assert n32 >= 3 * 128 * 96 * 4        # two state buffers + solve scratch
+    o64 = V.vp_opts(V.VP_FP64, 0, 0, 0, 0, 0, None)
+    n64 = V.vp_workspace_size(g, b, pu, o64)
+    assert n64 > n32
+    tent = V.vp_workspace_size(g, V.VP_BASIS_TENT, pu, o)
+    assert tent < n32                      # no Lambda^{-1} scratch for the tent deposit
+
+
+@pytest.mark.parametrize("bad", ["small_grid", "bad_basis", "bad_kind", "bad_precision",
+                                 "period", "tiles", "nan_dt", "huge_row"])
+def test_invalid_arguments_are_rejected_on_the_host(lib, bad):
+    g, b, pu, o = _cfg()
+    if bad == "small_grid":
+        g.nx = 3
+    elif bad == "bad_basis":
+        b = 7
+    elif bad == "bad_kind":
+        pu.kind = 9
+    elif bad == "bad_precision":
+        o.precision = 5
+    elif bad == "period":
+        g.x1 = 2.0                         # pendulum needs a 2 pi multiple period
+    elif bad == "tiles":
+        o.tile_x = 4096
+        o.tile_p = 4096
+        g.nx, g.np = 8192, 8192
+    elif bad == "nan_dt":
+        pu.dt = float("nan")
+    elif bad == "huge_row":
+        g.nx, g.np = 65536, 64             # cyclic row solve keeps a row in shared memory
+    n = C.c_size_t()
+    st = lib.vp_workspace_size(C.byref(g), b, C.byref(pu), C.byref(o), C.byref(n))
+    assert st in (V.VP_ERR_ARG, V.VP_ERR_UNSUPPORTED)
+
+
+def test_create_rejects_missing_workspace(lib):
+    g, b, pu, o = _cfg()
+    h = C.c_void_p()
+    st = lib.vp_create(C.byref(g), b, C.byref(pu), C.byref(o), None, 0, C.byref(h))
+    assert st == V.VP_ERR_WORKSPACE and not h.value
+
+
+def test_status_strings(lib):
+    for s in range(8):
+        assert lib.vp_status_string(s)
+    assert lib.vp_last_error(None) == b"NULL simulation"
+
+
+def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
+    monkeypatch.setattr(V, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(V, "_lib", None)
+    with pytest.raises(RuntimeError):
+        V.lib()
