@@ -1,0 +1,340 @@
+#!/usr/bin/env python
+"""Benchmark of the phase-space Vlasov step on GB300.
+
+Default workload: pendulum H = p^2/2 - cos x on an 8192 x 8192 mesh, FP32
+weights, cubic B-spline deposit with the Galerkin mass-matrix solve
+(tent basis), leapfrog dt = 0.02; one benchmark step = one vp_step(1):
+push + deposit + Lambda^{-1} (x and p solves) + step bookkeeping.
+
+Prints one JSON line. value = node-updates/s over all ranks (each rank runs
+an independent replica: the step has no cross-GPU exchange at this size).
+--impl reference times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2007_12227_gb300 import inputs as I  # noqa: E402
+
+METRIC = "phase-space node-updates/s (push+deposit) and HBM GB/s vs peak; batched/served vs plain"
+UNIT = "node-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--skip-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-extra", action="store_true")
+    ap.add_argument("--size", type=int, default=8192, help="mesh side (default 8192)")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload(size):
+    return I.pendulum_8192_fp32_cubic(size, size)
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def traffic_from_profile(kernel_file, source_files):
+    """Per-launch DRAM bytes from the committed ncu summary, if the kernel is unchanged."""
+    path = os.path.join(ROOT, "profiles", kernel_file)
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
+    if not m or not h:
+        return None
+    digest = hashlib.sha256()
+    for sf in source_files:
+        digest.update(open(os.path.join(ROOT, sf), "rb").read())
+    if digest.hexdigest() != h.group(1):
+        return None
+    return float(m.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, n in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def cpu_baseline(wl):
+    """The FP64 oracle, one step of the full mesh, single thread (a bounded sample)."""
+    from oracle import oracle as O
+    f0 = I.make_f0(wl)
+    O.lib()
+    t0 = time.perf_counter()
+    O.step(wl.grid, wl.basis, I.PROJ_GALERKIN, wl.pusher, f0)
+    dt = time.perf_counter() - t0
+    return {"value": wl.grid.nodes / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 step of the full {wl.grid.nx}x{wl.grid.np} mesh, FP64 serial C oracle, "
+                      f"{dt:.2f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    side = 2048
+    wl = workload(side)
+    f = I.make_f0(wl)
+    O.lib()
+    for _ in range(args.warmup):
+        f, _, _ = O.step(wl.grid, wl.basis, I.PROJ_GALERKIN, wl.pusher, f)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        f, _, _ = O.step(wl.grid, wl.basis, I.PROJ_GALERKIN, wl.pusher, f)
+    dt = time.perf_counter() - t0
+    value = wl.grid.nodes * args.steps / dt
+    sample = (f"{args.steps} steps of the same physics on a {side}x{side} mesh "
+              f"(FP64 serial C oracle; full mesh is 8192x8192)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name.replace(f"{side}x{side}", "8192x8192"),
+                       "sample_mesh": f"{side}x{side}", "steps": args.steps},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_2007_12227_gb300 import build as B
+    from paper_2007_12227_gb300 import vlasov as V
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    wl = workload(args.size)
+    g = wl.grid
+    N = g.nodes
+    f0 = I.make_f0(wl).astype(np.float32)
+    stream = torch.cuda.Stream()
+    sim = V.Sim(g, wl.basis, wl.pusher, precision=V.VP_FP32, stream=stream)
+    sim.set_f(f0)
+    sim.step(args.warmup)
+    sim.sync()
+
+    # ---- timed region: exactly K steps, events on the sim's stream
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    sim.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = ev0.elapsed_time(ev1)
+    sim.sync()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = ws * N * args.steps / (ms * 1e-3)
+
+    # ---- per-phase device time (same stream, events between the kernels)
+    nprof = min(args.steps, 500)
+    phase = sim.step_profiled(nprof)
+    phase_ms = [p / nprof for p in phase]
+    names = ["push_deposit", "lambda_inv_x", "lambda_inv_p", "field_or_count"]
+    dom = int(np.argmax(phase_ms))
+    bytes_per_node = {"push_deposit": 8, "lambda_inv_x": 8, "lambda_inv_p": 8,
+                      "field_or_count": 0}
+    peak, peak_kind = peaks()
+    alg_bytes = bytes_per_node[names[dom]] * N
+    achieved = alg_bytes / (phase_ms[dom] * 1e-3) / 1e9
+    kernel_files = {"push_deposit": ("step_tiled_pendulum_8192.md",
+                                     ["paper_2007_12227_gb300/csrc/vp_step.cu",
+                                      "paper_2007_12227_gb300/csrc/vp_internal.h"]),
+                    "lambda_inv_x": ("filter_x_pendulum_8192.md",
+                                     ["paper_2007_12227_gb300/csrc/vp_filter.cu"]),
+                    "lambda_inv_p": ("filter_p_pendulum_8192.md",
+                                     ["paper_2007_12227_gb300/csrc/vp_filter.cu"])}
+    traffic = None
+    if names[dom] in kernel_files:
+        traffic = traffic_from_profile(*kernel_files[names[dom]])
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": names[dom],
+                "peak_source": f"{peak_kind} hbm_gbs",
+                "algorithmic_bytes_per_launch": alg_bytes,
+                "phase_ms": dict(zip(names, phase_ms)),
+                "step_algorithmic_gbs": 8 * N / (ms_per_step * 1e-3) / 1e9,
+                "step_frac": 8 * N / (ms_per_step * 1e-3) / 1e9 / peak}
+
+    # ---- end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.skip_e2e:
+        host_in = torch.from_numpy(f0).pin_memory()
+        host_out = torch.empty_like(host_in).pin_memory()
+        ke = max(3, min(20, args.steps))
+        sim.set_f_host_ptr(host_in.data_ptr(), V.VP_FP32)
+        sim.step(1)
+        sim.get_f_host_ptr(host_out.data_ptr(), V.VP_FP32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            sim.set_f_host_ptr(host_in.data_ptr(), V.VP_FP32)
+            sim.step(1)
+            sim.get_f_host_ptr(host_out.data_ptr(), V.VP_FP32)
+        wall = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([wall], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            wall = float(t.item())
+        e2e = {"value": ws * N * ke / wall, "unit": UNIT, "h2d_bytes_per_step": 4 * N,
+               "d2h_bytes_per_step": 4 * N, "steps": ke,
+               "note": "per step: vp_set_f from pinned host + vp_step(1) + vp_get_f to pinned host"}
+
+    # ---- other workloads on the same GPU (context lines, not the headline)
+    extra = {}
+    if not args.skip_extra and rank == 0:
+        fel = I.fel_4096x2048_fp32_cubic()
+        fsim = V.Sim(fel.grid, fel.basis, fel.pusher, precision=V.VP_FP32, stream=stream)
+        fsim.set_f(I.make_f0(fel).astype(np.float32))
+        fsim.step(20)
+        fsim.sync()
+        nf = 500
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fsim.step(nf)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        fms = e0.elapsed_time(e1) / nf
+        extra[fel.name] = {"node_updates_per_s": fel.grid.nodes / (fms * 1e-3),
+                           "ms_per_step": fms, "steps_timed": nf,
+                           "phase_ms": dict(zip(names, [p / 200 for p in fsim.step_profiled(200)]))}
+        fsim.close()
+
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        cpu = cpu_baseline(wl)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32", "data": "synthetic",
+                "config": {"workload": wl.name, "mesh": f"{g.nx}x{g.np}", "dt": wl.pusher.dt,
+                           "basis": "cubic_bspline_galerkin", "parallelism": f"replicas{ws}",
+                           "l2": "inputs larger than L2 (two 256 MiB state buffers + 256 MiB solve scratch)"},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "gpu_launches": 4 * args.steps, "extra": extra}
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -74,9 +74,10 @@ enum {
 
 /* Step-kernel choice. */
 enum {
-    VP_KERNEL_AUTO = 0,     /* planner's choice (tiled) */
-    VP_KERNEL_TILED = 1,    /* destination tiles in shared memory, one coalesced store */
-    VP_KERNEL_SCATTER = 2   /* one thread per source node, global atomics (reference path) */
+    VP_KERNEL_AUTO = 0,     /* planner's choice (fused when the mesh allows, else tiled) */
+    VP_KERNEL_TILED = 1,    /* deposit into shared-memory tiles; Lambda^{-1} in two more passes */
+    VP_KERNEL_SCATTER = 2,  /* one thread per source node, global atomics (reference path) */
+    VP_KERNEL_FUSED = 3     /* one pass: p solve + push + deposit + x solve per tile */
 };
 
 typedef struct vp_grid {
@@ -145,6 +146,15 @@ vp_status vp_set_f_device(vp_sim *sim, const void *dev, int32_t dtype, size_t n)
 
 /* Advance n steps: push + deposit (+ Lambda^{-1}) (+ FEL bunching and field). Asynchronous. */
 vp_status vp_step(vp_sim *sim, int32_t n);
+
+/* vp_step, with CUDA events recorded between the phases of every step on the
+ * sim's stream. phase_ms[k] (k < nphases <= VP_NPHASES) receives the summed
+ * device time of phase k over the n steps: 0 push + deposit (Delta^T w),
+ * 1 Lambda^{-1} along x, 2 Lambda^{-1} along p, 3 FEL bunching + field update
+ * (or the step counter). Phases a configuration does not run read 0.
+ * Synchronises the stream. n <= 4096. */
+#define VP_NPHASES 4
+vp_status vp_step_profiled(vp_sim *sim, int32_t n, double *phase_ms, int32_t nphases);
 
 /* Copy the weights out ([np][nx] in dtype). vp_get_f synchronises the stream. */
 vp_status vp_get_f(vp_sim *sim, void *host, int32_t dtype, size_t n);

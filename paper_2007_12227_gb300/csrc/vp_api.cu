@@ -28,14 +28,18 @@ constexpr int kMoutLen = 32;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t f0, f1, tmp, col, row, rowb, vcb, csx, ucol, vcol, piv, state, hist, lost, part, mpart,
-        mout, err, total;
+    size_t f0, f1, tmp, col, row, rowb, vcb, csx, ucol, vcol, piv, sigma, state, hist, lost, part,
+        mpart, mout, err, total;
 };
 
 struct Plan {
     Geometry g;
     int precision, projection, kernel, tx, tp, ntx, ntp, hist_cap, nlost, npart, nmblk, nblk;
     bool galerkin, fel;
+    // fused kernel: guard band, window stride, threads per CTA, whole-period tiles;
+    // state_s: the stored state is s = Lambda_x^{-1} r instead of the weights w
+    int G, ws, threads;
+    bool full_row, state_s;
     Layout L;
 };
 
@@ -76,7 +80,7 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
         return fail(msg, VP_ERR_ARG, "unknown precision %d", opts->precision);
     if (opts->projection != VP_PROJ_GALERKIN && opts->projection != VP_PROJ_LUMPED)
         return fail(msg, VP_ERR_ARG, "unknown projection %d", opts->projection);
-    if (opts->kernel < 0 || opts->kernel > 2) return fail(msg, VP_ERR_ARG, "unknown kernel %d", opts->kernel);
+    if (opts->kernel < 0 || opts->kernel > 3) return fail(msg, VP_ERR_ARG, "unknown kernel %d", opts->kernel);
     if (opts->tile_x < 0 || opts->tile_p < 0 || opts->history_cap < 0)
         return fail(msg, VP_ERR_ARG, "tile sizes and history capacity must be >= 0");
 
@@ -119,19 +123,60 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
         g.KV = -(2.0 * h / g.hp);
     }
 
+    g.m0 = hypot(g.alpha0, g.beta0);
+    g.phi0 = atan2(g.beta0, g.alpha0);
+
     P->precision = opts->precision;
     P->projection = opts->projection;
     P->galerkin = basis == VP_BASIS_CUBIC_BSPLINE && opts->projection == VP_PROJ_GALERKIN;
-    int kernel = opts->kernel;
-    if (kernel == VP_KERNEL_AUTO) {
-        kernel = VP_KERNEL_TILED;
-        if (pu->kind == VP_PUSH_EXACT_ROTATION && fabs(pu->omega * h) >= 0.5 * M_PI)
-            kernel = VP_KERNEL_SCATTER;
-    }
-    P->kernel = kernel;
     const size_t sz = opts->precision == VP_FP64 ? 8 : 4;
+    const bool wide_rotation = pu->kind == VP_PUSH_EXACT_ROTATION && fabs(pu->omega * h) >= 0.5 * M_PI;
+    int kernel = opts->kernel;
+    P->G = 8;
+    P->full_row = false;
+    P->ws = 0;
+    P->threads = 0;
+    int ftx = 0, ftp = 0;
+    if (kernel == VP_KERNEL_AUTO || kernel == VP_KERNEL_FUSED) {
+        const int halo = P->galerkin ? fused_halo(opts->precision) : 0;
+        const int R = basis == VP_BASIS_TENT ? 1 : 2;
+        const int G = P->G;
+        ftx = opts->tile_x ? opts->tile_x : (opts->precision == VP_FP64 ? 128 : 224);
+        ftp = opts->tile_p ? opts->tile_p : 64;
+        bool full = false;
+        if (grid->nx <= kFusedMaxRow && grid->nx < ftx + 2 * halo + 2 * G + 64) {
+            full = true;
+            ftx = grid->nx;
+        }
+        if (!full && ftx + 2 * halo > kFusedMaxRow) ftx = kFusedMaxRow - 2 * halo;
+        ftp = std::min(ftp, grid->np);
+        const int WW = full ? grid->nx + 2 * G : ftx + 2 * halo + 2 * G;
+        const int ws = (WW + 31) / 32 * 32 + 1;
+        while ((size_t)ws * (ftp + 2 * G) * sz > 110 * 1024 && ftp > 8) ftp /= 2;
+        const size_t smem = (size_t)ws * (ftp + 2 * G) * sz;
+        const bool ok = !wide_rotation && smem <= kMaxSmem && (full || WW < grid->nx) && ftx >= 1;
+        if (ok) {
+            kernel = VP_KERNEL_FUSED;
+            P->full_row = full;
+            P->ws = ws;
+            const int wsrc = (full ? grid->nx : ftx + 2 * halo) + 2 * R + 8;
+            P->threads = std::min(kFusedMaxThreads, (wsrc + 31) / 32 * 32);
+        } else if (kernel == VP_KERNEL_FUSED) {
+            return fail(msg, VP_ERR_UNSUPPORTED,
+                        "the fused kernel needs a mesh wider than its window (nx = %d)", grid->nx);
+        } else {
+            kernel = VP_KERNEL_TILED;
+        }
+    }
+    if (kernel == VP_KERNEL_TILED && wide_rotation) kernel = VP_KERNEL_SCATTER;
+    P->kernel = kernel;
+    P->state_s = kernel == VP_KERNEL_FUSED && P->galerkin;
     int tx = opts->tile_x ? opts->tile_x : (opts->precision == VP_FP64 ? 64 : 128);
     int tp = opts->tile_p ? opts->tile_p : 64;
+    if (kernel == VP_KERNEL_FUSED) {
+        tx = ftx;
+        tp = ftp;
+    }
     tx = std::min(tx, grid->nx);
     tp = std::min(tp, grid->np);
     if (tx > 4096 || tp > 4096) return fail(msg, VP_ERR_ARG, "tile sides must be <= 4096");
@@ -153,7 +198,7 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     P->ntx = (grid->nx + tx - 1) / tx;
     P->ntp = (grid->np + tp - 1) / tp;
     P->hist_cap = opts->history_cap ? opts->history_cap : kDefaultHist;
-    P->nlost = kernel == VP_KERNEL_TILED ? P->ntx * P->ntp : 1;
+    P->nlost = (kernel == VP_KERNEL_TILED || kernel == VP_KERNEL_FUSED) ? P->ntx * P->ntp : 1;
     P->npart = std::max(std::max(filter_p_blocks(grid->nx, grid->np), P->ntx * P->ntp),
                         fel_partial_blocks(grid->nx, grid->np));
     P->nmblk = moment_blocks(grid->nx, grid->np);
@@ -180,6 +225,7 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     L.ucol = take(grid->nx * sizeof(double));
     L.vcol = take(grid->nx * sizeof(double));
     L.piv = take((2 * kPivots + 2) * sizeof(double));
+    L.sigma = take(grid->np * sizeof(double));
     L.state = take(ST_NSTATE * sizeof(double));
     L.hist = take((size_t)P->hist_cap * 2 * sizeof(double));
     L.lost = take(P->nlost * sizeof(double));
@@ -249,6 +295,53 @@ StepArgs<T> step_args(vp_sim *s, const void *src, void *dst)
 }
 
 template <typename T>
+FusedArgs<T> fused_args(vp_sim *s, const void *src, void *dst)
+{
+    const Plan &P = s->P;
+    FusedArgs<T> a;
+    a.src = static_cast<const T *>(src);
+    a.dst = static_cast<T *>(dst);
+    a.col = s->ptr<ColEntry<T>>(P.L.col);
+    a.row = s->ptr<RowEntry<T>>(P.L.row);
+    a.rowb = s->ptr<RowBound>(P.L.rowb);
+    a.vcb = s->ptr<double>(P.L.vcb);
+    a.state = s->ptr<double>(P.L.state);
+    a.piv = s->ptr<double>(P.L.piv);
+    a.sigma = s->ptr<double>(P.L.sigma);
+    a.csx = s->ptr<double2>(P.L.csx);
+    a.tile_lost = s->ptr<double>(P.L.lost);
+    a.tile_part = s->ptr<double>(P.L.part);
+    a.err = s->ptr<unsigned>(P.L.err);
+    a.g = P.g;
+    a.tx = P.tx;
+    a.tp = P.tp;
+    a.ntx = P.ntx;
+    a.ntp = P.ntp;
+    a.G = P.G;
+    a.ws = P.ws;
+    a.full_row = P.full_row ? 1 : 0;
+    a.fel_partials = P.fel ? 1 : 0;
+    return a;
+}
+
+// the weights w of the current state: the state itself, or Lambda_p^{-1} s in scratch
+template <typename T>
+vp_status weights_of_state(vp_sim *s, const void **w)
+{
+    const Plan &P = s->P;
+    if (!P.state_s) {
+        *w = s->f(s->cur);
+        return VP_OK;
+    }
+    T *tmp = s->ptr<T>(P.L.tmp);
+    VP_CUDA(s, launch_filter_p<T>(static_cast<const T *>(s->f(s->cur)), tmp, P.g.nx, P.g.np,
+                                  s->ptr<double>(P.L.piv), s->ptr<double2>(P.L.csx),
+                                  s->ptr<double>(P.L.part), 0, s->ptr<unsigned>(P.L.err), s->stream));
+    *w = tmp;
+    return VP_OK;
+}
+
+template <typename T>
 vp_status fel_bunching(vp_sim *s, const void *w, int init)
 {
     const Plan &P = s->P;
@@ -260,8 +353,9 @@ vp_status fel_bunching(vp_sim *s, const void *w, int init)
     return VP_OK;
 }
 
+// ev (optional): VP_NPHASES + 1 events per step, recorded at the phase boundaries
 template <typename T>
-vp_status do_steps(vp_sim *s, int n)
+vp_status do_steps(vp_sim *s, int n, cudaEvent_t *ev = nullptr)
 {
     const Plan &P = s->P;
     const size_t N = (size_t)P.g.nx * P.g.np;
@@ -269,22 +363,31 @@ vp_status do_steps(vp_sim *s, int n)
     double *state = s->ptr<double>(P.L.state);
     unsigned *err = s->ptr<unsigned>(P.L.err);
     for (int k = 0; k < n; ++k) {
+        cudaEvent_t *e = ev ? ev + (size_t)k * (VP_NPHASES + 1) : nullptr;
+        if (e) VP_CUDA(s, cudaEventRecord(e[0], s->stream));
         void *src = s->f(s->cur), *dst = s->f(1 - s->cur);
         StepArgs<T> a = step_args<T>(s, src, dst);
-        if (P.kernel == VP_KERNEL_TILED) {
+        if (P.kernel == VP_KERNEL_FUSED) {
+            VP_CUDA(s, launch_step_fused<T>(fused_args<T>(s, src, dst), P.threads, s->stream));
+        } else if (P.kernel == VP_KERNEL_TILED) {
             VP_CUDA(s, launch_step_tiled<T>(a, s->stream));
         } else {
             VP_CUDA(s, cudaMemsetAsync(dst, 0, N * sizeof(T), s->stream));
             VP_CUDA(s, launch_step_scatter<T>(a, s->ptr<double>(P.L.lost), s->stream));
         }
+        if (e) VP_CUDA(s, cudaEventRecord(e[1], s->stream));
         int nparts = 0;
-        if (P.galerkin) {
+        if (P.kernel == VP_KERNEL_FUSED) {
+            nparts = P.ntx * P.ntp;
+        } else if (P.galerkin) {
             T *tmp = s->ptr<T>(P.L.tmp);
             VP_CUDA(s, launch_filter_x<T>(static_cast<const T *>(dst), tmp, P.g.nx, P.g.np, err,
                                           s->stream));
+            if (e) VP_CUDA(s, cudaEventRecord(e[2], s->stream));
             VP_CUDA(s, launch_filter_p<T>(tmp, static_cast<T *>(dst), P.g.nx, P.g.np,
                                           s->ptr<double>(P.L.piv), s->ptr<double2>(P.L.csx), part,
                                           P.fel ? 1 : 0, err, s->stream));
+            if (e) VP_CUDA(s, cudaEventRecord(e[3], s->stream));
             nparts = filter_p_blocks(P.g.nx, P.g.np);
         } else if (P.fel) {
             if (P.kernel == VP_KERNEL_TILED) {
@@ -295,18 +398,23 @@ vp_status do_steps(vp_sim *s, int n)
                 nparts = fel_partial_blocks(P.g.nx, P.g.np);
             }
         }
+        if (e && (!P.galerkin || P.kernel == VP_KERNEL_FUSED)) {
+            VP_CUDA(s, cudaEventRecord(e[2], s->stream));
+            VP_CUDA(s, cudaEventRecord(e[3], s->stream));
+        }
         if (P.fel) {
             VP_CUDA(s, launch_fel_finalize(part, nparts, state, s->ptr<double>(P.L.hist), P.hist_cap,
                                            P.g.dt, 0, s->stream));
         } else {
             VP_CUDA(s, launch_count_step(state, P.g.dt, s->stream));
         }
+        if (e) VP_CUDA(s, cudaEventRecord(e[4], s->stream));
         s->cur = 1 - s->cur;
     }
     return VP_OK;
 }
 
-vp_status reset_state(vp_sim *s)
+vp_status reset_state(vp_sim *s, const void *w)
 {
     const Plan &P = s->P;
     memset(s->host_state, 0, sizeof(s->host_state));
@@ -318,8 +426,8 @@ vp_status reset_state(vp_sim *s)
     VP_CUDA(s, cudaMemsetAsync(s->ws + P.L.err, 0, sizeof(unsigned), s->stream));
     VP_CUDA(s, cudaMemsetAsync(s->ws + P.L.hist, 0, (size_t)P.hist_cap * 2 * sizeof(double), s->stream));
     if (P.fel) {
-        vp_status st = P.precision == VP_FP64 ? fel_bunching<double>(s, s->f(s->cur), 1)
-                                              : fel_bunching<float>(s, s->f(s->cur), 1);
+        vp_status st = P.precision == VP_FP64 ? fel_bunching<double>(s, w, 1)
+                                              : fel_bunching<float>(s, w, 1);
         if (st != VP_OK) return st;
     }
     // the host copy above reads host_state: finish it before the struct is reused
@@ -448,6 +556,24 @@ vp_status vp_create(const vp_grid *grid, int32_t basis, const vp_pusher *pusher,
     const double beta_inf = 1.0 / 3.0 + 1.0 / (2.0 * sqrt(3.0));
     piv[2 * kPivots] = (1.0 / 6.0) / beta_inf;
     piv[2 * kPivots + 1] = 1.0 / beta_inf;
+    // sigma = column sums of Lambda_p^{-1} (np x np tridiag(1/6, 2/3, 1/6), symmetric):
+    // the Thomas solve of T sigma = 1
+    std::vector<double> sigma(g.np, 1.0), cpv(g.np);
+    {
+        double beta = 2.0 / 3.0;
+        cpv[0] = (1.0 / 6.0) / beta;
+        sigma[0] = sigma[0] / beta;
+        for (int j = 1; j < g.np; ++j) {
+            beta = 2.0 / 3.0 - (1.0 / 6.0) * cpv[j - 1];
+            cpv[j] = (1.0 / 6.0) / beta;
+            sigma[j] = (sigma[j] - (1.0 / 6.0) * sigma[j - 1]) / beta;
+        }
+        for (int j = g.np - 2; j >= 0; --j) sigma[j] -= cpv[j] * sigma[j + 1];
+    }
+    e = cudaMemcpyAsync(s->ws + P.L.sigma, sigma.data(), sigma.size() * sizeof(double),
+                        cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cleanup(cuda_fail(nullptr, e, "sigma upload"));
     e = cudaMemcpyAsync(s->ws + P.L.vcb, vcb.data(), vcb.size() * sizeof(double),
                         cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess)
@@ -468,7 +594,8 @@ static vp_status set_f_common(vp_sim *s, const void *src, int32_t dtype, size_t 
     if (!src || n != N || (dtype != VP_FP32 && dtype != VP_FP64))
         return fail(s->msg, VP_ERR_ARG, "set_f: need %zu values of dtype FP32/FP64", N);
     s->cur = 0;
-    void *dst = s->f(0);
+    // the weights go to the state buffer, or to scratch when the state is s = Lambda_p w
+    void *dst = P.state_s ? (void *)(s->ws + P.L.tmp) : s->f(0);
     const size_t szs = P.precision == VP_FP64 ? 8 : 4;
     if (dtype == P.precision) {
         VP_CUDA(s, cudaMemcpyAsync(dst, src, N * szs,
@@ -496,7 +623,19 @@ static vp_status set_f_common(vp_sim *s, const void *src, int32_t dtype, size_t 
         VP_CUDA(s, cudaStreamSynchronize(s->stream));
     }
     s->f_set = true;
-    return reset_state(s);
+    vp_status st = reset_state(s, dst);
+    if (st != VP_OK) return st;
+    if (P.state_s) {
+        if (P.precision == VP_FP64)
+            VP_CUDA(s, launch_lambda_p_mul<double>(static_cast<const double *>(dst),
+                                                   static_cast<double *>(s->f(0)), P.g.nx, P.g.np,
+                                                   s->stream));
+        else
+            VP_CUDA(s, launch_lambda_p_mul<float>(static_cast<const float *>(dst),
+                                                  static_cast<float *>(s->f(0)), P.g.nx, P.g.np,
+                                                  s->stream));
+    }
+    return VP_OK;
 }
 
 vp_status vp_set_f(vp_sim *s, const void *host, int32_t dtype, size_t n)
@@ -517,6 +656,43 @@ vp_status vp_step(vp_sim *s, int32_t n)
     return s->P.precision == VP_FP64 ? do_steps<double>(s, n) : do_steps<float>(s, n);
 }
 
+vp_status vp_step_profiled(vp_sim *s, int32_t n, double *phase_ms, int32_t nphases)
+{
+    if (!s) return VP_ERR_ARG;
+    if (n < 0 || n > 4096 || !phase_ms || nphases < 1 || nphases > VP_NPHASES)
+        return fail(s->msg, VP_ERR_ARG, "vp_step_profiled: 0 <= n <= 4096, 1 <= nphases <= %d",
+                    VP_NPHASES);
+    if (!s->f_set) return fail(s->msg, VP_ERR_STATE, "vp_step before vp_set_f");
+    const size_t ne = (size_t)n * (VP_NPHASES + 1);
+    std::vector<cudaEvent_t> ev(ne, nullptr);
+    vp_status st = VP_OK;
+    for (size_t k = 0; k < ne && st == VP_OK; ++k) {
+        cudaError_t e = cudaEventCreate(&ev[k]);
+        if (e != cudaSuccess) st = cuda_fail(s, e, "cudaEventCreate");
+    }
+    if (st == VP_OK)
+        st = s->P.precision == VP_FP64 ? do_steps<double>(s, n, ev.data()) : do_steps<float>(s, n, ev.data());
+    if (st == VP_OK) {
+        cudaError_t e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) st = cuda_fail(s, e, "cudaStreamSynchronize");
+    }
+    for (int q = 0; q < nphases; ++q) phase_ms[q] = 0.0;
+    for (int k = 0; k < n && st == VP_OK; ++k)
+        for (int q = 0; q < nphases; ++q) {
+            float ms = 0.f;
+            cudaError_t e = cudaEventElapsedTime(&ms, ev[(size_t)k * (VP_NPHASES + 1) + q],
+                                                 ev[(size_t)k * (VP_NPHASES + 1) + q + 1]);
+            if (e != cudaSuccess) {
+                st = cuda_fail(s, e, "cudaEventElapsedTime");
+                break;
+            }
+            phase_ms[q] += ms;
+        }
+    for (cudaEvent_t e : ev)
+        if (e) cudaEventDestroy(e);
+    return st;
+}
+
 static vp_status get_f_common(vp_sim *s, void *dstp, int32_t dtype, size_t n, bool device)
 {
     if (!s) return VP_ERR_ARG;
@@ -525,7 +701,12 @@ static vp_status get_f_common(vp_sim *s, void *dstp, int32_t dtype, size_t n, bo
     if (!dstp || n != N || (dtype != VP_FP32 && dtype != VP_FP64))
         return fail(s->msg, VP_ERR_ARG, "get_f: need room for %zu values of dtype FP32/FP64", N);
     if (!s->f_set) return fail(s->msg, VP_ERR_STATE, "vp_get_f before vp_set_f");
-    const void *src = s->f(s->cur);
+    const void *src = nullptr;
+    {
+        vp_status st = P.precision == VP_FP64 ? weights_of_state<double>(s, &src)
+                                              : weights_of_state<float>(s, &src);
+        if (st != VP_OK) return st;
+    }
     const size_t szs = P.precision == VP_FP64 ? 8 : 4;
     if (dtype == P.precision) {
         VP_CUDA(s, cudaMemcpyAsync(dstp, src, N * szs,
@@ -573,11 +754,17 @@ vp_status vp_moments(vp_sim *s, vp_moments_t *out)
     const Plan &P = s->P;
     double *mpart = s->ptr<double>(P.L.mpart);
     double *mout = s->ptr<double>(P.L.mout);
+    const void *w = nullptr;
+    {
+        vp_status st = P.precision == VP_FP64 ? weights_of_state<double>(s, &w)
+                                              : weights_of_state<float>(s, &w);
+        if (st != VP_OK) return st;
+    }
     if (P.precision == VP_FP64)
-        VP_CUDA(s, launch_moments<double>(static_cast<const double *>(s->f(s->cur)), P.g,
+        VP_CUDA(s, launch_moments<double>(static_cast<const double *>(w), P.g,
                                           s->ptr<double2>(P.L.csx), mpart, P.nmblk, s->stream));
     else
-        VP_CUDA(s, launch_moments<float>(static_cast<const float *>(s->f(s->cur)), P.g,
+        VP_CUDA(s, launch_moments<float>(static_cast<const float *>(w), P.g,
                                          s->ptr<double2>(P.L.csx), mpart, P.nmblk, s->stream));
     VP_CUDA(s, launch_moments_finalize(mpart, P.nmblk, s->ptr<double>(P.L.lost), P.nlost, mout,
                                        s->stream));
@@ -651,8 +838,12 @@ vp_status vp_set_stream(vp_sim *s, void *stream)
 vp_status vp_state_device(vp_sim *s, void **dev)
 {
     if (!s || !dev) return VP_ERR_ARG;
-    *dev = s->f(s->cur);
-    return VP_OK;
+    if (!s->f_set) return fail(s->msg, VP_ERR_STATE, "vp_state_device before vp_set_f");
+    const void *w = nullptr;
+    vp_status st = s->P.precision == VP_FP64 ? weights_of_state<double>(s, &w)
+                                             : weights_of_state<float>(s, &w);
+    *dev = const_cast<void *>(w);
+    return st;
 }
 
 void vp_destroy(vp_sim *s) { delete s; }

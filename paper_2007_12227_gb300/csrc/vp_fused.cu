@@ -1,0 +1,770 @@
+// vp_fused.cu -- one-pass step: [Lambda_p^{-1}] + push + deposit + [Lambda_x^{-1}].
+//
+// Sec. III update w_fin = Lambda^{-1} Delta^T w_in with Lambda = Lambda_x (x) Lambda_p
+// (tent basis). In cubic B-spline Galerkin mode the library keeps, between
+// steps, s = Lambda_x^{-1} r where r = Delta^T w is the deposit; one step is then
+//   w  = Lambda_p^{-1} s         (per column, on the source side)
+//   r' = Delta^T w               (push every node, deposit with the B3 kernel)
+//   s' = Lambda_x^{-1} r'        (per row, on the destination side)
+// so each step reads and writes the mesh once. With the tent deposit or the
+// lumped projection there is no solve and the state is w itself.
+//
+// One CTA owns one destination tile [X0, X0+TX) x [P0, P0+TP). It keeps a
+// shared-memory window: the tile widened by the x-solve halo D and a guard
+// band G. It bounds the source nodes whose pushed B3 footprint reaches the
+// widened tile and gives each thread one source column. The thread walks the
+// column:
+//   * Galerkin: the p solve is the Thomas sweep of tridiag(1/6, 2/3, 1/6)
+//     (exact pivots near row 0): the forward sweep runs into a register ring,
+//     the back substitution runs over chunks of kChunk rows with kHalo rows
+//     of look-ahead (truncation |z|^kHalo, z = sqrt(3) - 2);
+//   * every node is pushed (displacement tables, vp_internal.h) and its N x N
+//     taps accumulate in an N x N register ring that follows the node's base
+//     row; when the ring moves one row, the row that leaves it is added to the
+//     window with N shared-memory atomics.
+// Contributions outside the window belong to other tiles, except rows beyond
+// the open momentum edge, which are counted as lost by the tile owning the
+// column. Finally each warp takes window rows, solves Lambda_x along them
+// (first-order recurrences combined across lanes with a warp scan), and the
+// tile is stored once.
+#include <math.h>
+
+#include "vp_internal.h"
+
+namespace vp {
+namespace {
+
+// look-ahead / x-solve halo: |z|^14 = 1e-8 (FP32), |z|^28 = 1e-16 (FP64)
+template <typename T>
+struct Halo {
+    static constexpr int value = sizeof(T) == 4 ? 14 : 28;
+};
+constexpr int kChunk = 16;          // rows per backward sweep
+constexpr int kXMax = kFusedMaxRow / 32;
+
+template <typename T, int BASIS>
+struct FTaps;
+
+template <typename T>
+struct FTaps<T, VP_BASIS_TENT> {
+    static constexpr int N = 2;
+    static constexpr int LO = 0;
+    __device__ __forceinline__ static void weights(T t, T *w)
+    {
+        w[0] = T(1) - t;
+        w[1] = t;
+    }
+};
+
+template <typename T>
+struct FTaps<T, VP_BASIS_CUBIC_BSPLINE> {
+    static constexpr int N = 4;
+    static constexpr int LO = -1;
+    // cubic B-spline at offsets 1+t, t, 1-t, 2-t
+    __device__ __forceinline__ static void weights(T t, T *w)
+    {
+        const T s = T(1) - t;
+        const T t2 = t * t, s2 = s * s;
+        const T t3 = t2 * t, s3 = s2 * s;
+        const T sixth = T(1) / T(6), two3 = T(2) / T(3);
+        w[0] = s3 * sixth;
+        w[3] = t3 * sixth;
+        w[1] = two3 - t2 + T(0.5) * t3;
+        w[2] = two3 - s2 + T(0.5) * s3;
+    }
+};
+
+__device__ __forceinline__ int imod(int a, int n)
+{
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+// z^n for the pole z = sqrt(3) - 2 < 0
+template <typename T>
+__device__ __forceinline__ T zpow(int n);
+
+template <>
+__device__ __forceinline__ float zpow<float>(int n)
+{
+    // log2|z| = log2(2 - sqrt(3))
+    const float m = exp2f((float)n * -1.8999686269529425f);
+    return (n & 1) ? -m : m;
+}
+
+template <>
+__device__ __forceinline__ double zpow<double>(int n)
+{
+    const double m = exp2((double)n * -1.8999686269529425);
+    return (n & 1) ? -m : m;
+}
+
+// range of sin over [lo, hi]: FP64 reduction, FP32 evaluation, 1e-5 slack
+__device__ void sin_range_f(double lo, double hi, float &smin, float &smax)
+{
+    const double twopi = 6.283185307179586476925286766559;
+    if (hi - lo >= twopi) {
+        smin = -1.f;
+        smax = 1.f;
+        return;
+    }
+    const double k = floor(lo / twopi);
+    const double a = lo - k * twopi, b = hi - k * twopi;
+    const float sa = sinf((float)a), sb = sinf((float)b);
+    smin = fminf(sa, sb) - 1e-5f;
+    smax = fmaxf(sa, sb) + 1e-5f;
+    const double h1 = 1.5707963267948966, h3 = 4.7123889803846897;
+    if ((a <= h1 && h1 <= b) || (a <= h1 + twopi && h1 + twopi <= b)) smax = 1.f;
+    if ((a <= h3 && h3 <= b) || (a <= h3 + twopi && h3 + twopi <= b)) smin = -1.f;
+}
+
+template <typename T>
+__device__ __forceinline__ void kahan(T &sum, T &comp, T v)
+{
+    const T y = v - comp;
+    const T t = sum + y;
+    comp = (t - sum) - y;
+    sum = t;
+}
+
+template <typename T, int N>
+struct Ring {
+    T acc[N][N];
+    int mref;     // window column of tap a = 0
+    int nb;       // window row of tap b = 0 of the last node
+    bool col_ok;  // all N columns inside the window
+    bool live;
+};
+
+struct WinGeom {
+    int WW, WH, ws;      // window width, height, row stride (elements)
+    int WX0, WP0;        // grid column (unwrapped) and row of window cell (0, 0)
+    int own_c0, own_c1;  // the tile's own columns, window coordinates [c0, c1)
+    int np, nx, G;
+    bool full;           // the tile spans the whole period
+};
+
+template <typename T, int N>
+__device__ __forceinline__ void flush_row(T *win, const WinGeom &W, const T *acc, int mref,
+                                          bool col_ok, int row, double &lost)
+{
+    if (row >= 0 && row < W.WH && col_ok) {
+        T *p = win + row * W.ws + mref;
+#pragma unroll
+        for (int a = 0; a < N; ++a) atomicAdd(p + a, acc[a]);
+        return;
+    }
+    const int grow = row + W.WP0;
+    const bool outside = grow < 0 || grow >= W.np;
+    const bool rin = row >= 0 && row < W.WH;
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+        int c = mref + a;
+        if (W.full && (c < 0 || c >= W.WW)) c = W.G + imod(c - W.G, W.nx);   // wrap onto the period
+        if (c >= 0 && c < W.WW) {
+            if (rin) atomicAdd(win + row * W.ws + c, acc[a]);
+            else if (outside && (W.full || (c >= W.own_c0 && c < W.own_c1))) lost += (double)acc[a];
+        } else if (outside && W.full) {
+            lost += (double)acc[a];
+        }
+    }
+}
+
+// Add one node (weights wx, wy; base window column m, row n) at static phase PH.
+// DIR = +1: base rows ascend between consecutive calls; DIR = -1: they descend.
+// Slot of tap row b: (b + PH) % N ascending, (b - PH) % N descending.
+template <typename T, int N, int DIR>
+__device__ __forceinline__ void ring_add(T *win, const WinGeom &W, Ring<T, N> &rg, int m, int n,
+                                         const T *wx, const T *wy, double &lost, const int PH)
+{
+    const int PHN = PH % N;
+    const int PP = (PH + N - 1) % N;   // phase of the previous node
+    if (!(rg.live && m == rg.mref && n == rg.nb + DIR)) {
+        if (rg.live) {
+#pragma unroll
+            for (int b = 0; b < N; ++b) {
+                const int q = DIR > 0 ? (b + PP) % N : (b - PP + N) % N;
+                flush_row<T, N>(win, W, rg.acc[q], rg.mref, rg.col_ok, rg.nb + b, lost);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < N; ++q)
+#pragma unroll
+            for (int a = 0; a < N; ++a) rg.acc[q][a] = T(0);
+        rg.mref = m;
+        rg.col_ok = m >= 0 && m + N <= W.WW;
+        rg.live = true;
+    } else {
+        // the ring moves one row: the row leaving it is complete
+        const int q = DIR > 0 ? (PHN + N - 1) % N : (N - PHN) % N;
+        const int row = DIR > 0 ? rg.nb : rg.nb + N - 1;
+        flush_row<T, N>(win, W, rg.acc[q], rg.mref, rg.col_ok, row, lost);
+#pragma unroll
+        for (int a = 0; a < N; ++a) rg.acc[q][a] = T(0);
+    }
+    rg.nb = n;
+#pragma unroll
+    for (int b = 0; b < N; ++b) {
+        const int q = DIR > 0 ? (b + PHN) % N : (b - PHN + N) % N;
+#pragma unroll
+        for (int a = 0; a < N; ++a) rg.acc[q][a] += wy[b] * wx[a];
+    }
+}
+
+template <typename T, int N, int DIR>
+__device__ __forceinline__ void ring_final(T *win, const WinGeom &W, Ring<T, N> &rg, double &lost,
+                                           const int PH)
+{
+    if (!rg.live) return;
+    const int PHN = PH % N;
+#pragma unroll
+    for (int b = 0; b < N; ++b) {
+        const int q = DIR > 0 ? (b + PHN) % N : (b - PHN + N) % N;
+        flush_row<T, N>(win, W, rg.acc[q], rg.mref, rg.col_ok, rg.nb + b, lost);
+    }
+    rg.live = false;
+}
+
+template <typename T>
+struct ColC {
+    int ui, vi;
+    T uf, vf, cu1, cu2, cv1, cv2;
+};
+
+template <typename T, int BASIS, bool UTERM>
+__device__ __forceinline__ void node_taps(const ColC<T> &c, const RowEntry<T> &r, int colrel,
+                                          int rowrel, T w, int &m, int &n, T *wx, T *wy)
+{
+    using TP = FTaps<T, BASIS>;
+    T fu = c.uf + r.uf;
+    if (UTERM) fu += c.cu1 * r.cy + c.cu2 * r.sy;
+    const T fv = (c.vf + r.vf) + c.cv1 * r.cy + c.cv2 * r.sy;
+    const T flu = floor(fu), flv = floor(fv);
+    m = colrel + c.ui + r.ui + (int)flu + TP::LO;
+    n = rowrel + c.vi + r.vi + (int)flv + TP::LO;
+    TP::weights(fu - flu, wx);
+    TP::weights(fv - flv, wy);
+#pragma unroll
+    for (int b = 0; b < TP::N; ++b) wy[b] *= w;
+}
+
+// Lambda_x^{-1} (T x = row, T = tridiag(1/6, 2/3, 1/6)) of one row of length L held in
+// shared memory, by one warp. Returns each lane's elements base .. base + per - 1 in v.
+// cyclic: the row is one whole period; else the row is padded by the halo on both
+// sides and the recurrences start from zero at its ends (truncation |z|^halo).
+template <typename T>
+__device__ void solve_row_x(const T *row, int L, bool cyclic, int lane, T *v, int &per, int &base)
+{
+    per = (L + 31) / 32;
+    base = lane * per;
+    const T z = (T)-0.26794919243112270647;
+#pragma unroll
+    for (int k = 0; k < kXMax; ++k) v[k] = (k < per && base + k < L) ? row[base + k] : T(0);
+    const T zper = zpow<T>(per);
+    // causal y_i = x_i + z y_{i-1}: lane-local sweep, then carries by a warp scan
+    T y = T(0);
+#pragma unroll
+    for (int k = 0; k < kXMax; ++k)
+        if (k < per) {
+            y = v[k] + z * y;
+            v[k] = y;
+        }
+    T endv = y;
+    T zp = zper;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const T o = __shfl_up_sync(0xffffffffu, endv, off);
+        if (lane >= off) endv += zp * o;
+        zp *= zp;
+    }
+    T carry = __shfl_up_sync(0xffffffffu, endv, 1);
+    if (lane == 0) carry = T(0);
+    {
+        T zk = z;
+#pragma unroll
+        for (int k = 0; k < kXMax; ++k)
+            if (k < per) {
+                v[k] += zk * carry;
+                zk *= z;
+            }
+    }
+    if (cyclic) {
+        // y_{-1} = y_{L-1}: with E the zero-start value at L-1, y_{-1} = E / (1 - z^L)
+        const int ll = (L - 1) / per, kl = (L - 1) - ll * per;
+        T mine = T(0);
+#pragma unroll
+        for (int k = 0; k < kXMax; ++k)
+            if (k == kl) mine = v[k];
+        const T E = __shfl_sync(0xffffffffu, mine, ll);
+        const T yprev = E / (T(1) - zpow<T>(L));
+        T zk = zpow<T>(base + 1);
+#pragma unroll
+        for (int k = 0; k < kXMax; ++k)
+            if (k < per) {
+                v[k] += zk * yprev;
+                zk *= z;
+            }
+    }
+    // anticausal u_i = y_i + z u_{i+1}
+    int last = per - 1;
+    if (base + last >= L) last = L - 1 - base;   // may be negative for idle lanes
+    T u = T(0);
+#pragma unroll
+    for (int k = kXMax - 1; k >= 0; --k)
+        if (k <= last) {
+            u = v[k] + z * u;
+            v[k] = u;
+        }
+    T startv = u;
+    zp = zper;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const T o = __shfl_down_sync(0xffffffffu, startv, off);
+        if (lane + off < 32) startv += zp * o;
+        zp *= zp;
+    }
+    T carry2 = __shfl_down_sync(0xffffffffu, startv, 1);
+    if (lane == 31) carry2 = T(0);
+    {
+        T zk = z;
+#pragma unroll
+        for (int k = kXMax - 1; k >= 0; --k)
+            if (k <= last) {
+                v[k] += zk * carry2;
+                zk *= z;
+            }
+    }
+    if (cyclic) {
+        // u_L = u_0: with S the zero-end value at 0, u_L = S / (1 - z^L)
+        const T S = __shfl_sync(0xffffffffu, v[0], 0);
+        const T unext = S / (T(1) - zpow<T>(L));
+        // element i gets z^{L - i} u_L
+#pragma unroll
+        for (int k = 0; k < kXMax; ++k)
+            if (k <= last) v[k] += zpow<T>(L - (base + k)) * unext;
+    }
+    const T scale = T(-6) * z;
+#pragma unroll
+    for (int k = 0; k < kXMax; ++k) v[k] *= scale;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+template <typename T, int BASIS, bool GAL, bool UTERM>
+__global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const FusedArgs<T> A)
+{
+    using TP = FTaps<T, BASIS>;
+    constexpr int N = TP::N;
+    constexpr int R = (BASIS == VP_BASIS_TENT) ? 1 : 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *win = reinterpret_cast<T *>(smem_raw);
+    __shared__ int s_ia, s_ib, s_ja, s_jb;
+    __shared__ double s_r4[4][kFusedMaxThreads / 32];
+
+    const Geometry &g = A.g;
+    const int nx = g.nx, np = g.np;
+    const int tile = blockIdx.x;
+    const int tix = tile % A.ntx, tip = tile / A.ntx;
+    const int X0 = tix * A.tx, P0 = tip * A.tp;
+    const int TXe = min(A.tx, nx - X0), TPe = min(A.tp, np - P0);
+    const bool full = A.full_row != 0;
+    constexpr int kHalo = Halo<T>::value;
+    const int D = (GAL && !full) ? kHalo : 0;
+    const int G = A.G;
+    WinGeom W;
+    W.WW = full ? nx + 2 * G : TXe + 2 * D + 2 * G;
+    W.WH = TPe + 2 * G;
+    W.ws = A.ws;
+    W.WX0 = X0 - D - G;
+    W.WP0 = P0 - G;
+    W.own_c0 = G + D;
+    W.own_c1 = G + D + TXe;
+    W.np = np;
+    W.nx = nx;
+    W.G = G;
+    W.full = full;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+
+    for (int k = tid; k < W.WH * W.ws; k += blockDim.x) win[k] = T(0);
+    if (tid == 0) {
+        s_ia = 0x7fffffff;
+        s_ib = -0x7fffffff;
+        s_ja = 0x7fffffff;
+        s_jb = -0x7fffffff;
+    }
+    double al = g.alpha0, be = g.beta0, M = g.m0, phi = g.phi0;
+    if (g.kind == VP_PUSH_FEL_DKD) {
+        al = -A.state[ST_AH_IM];
+        be = A.state[ST_AH_RE];
+        M = A.state[ST_M];
+        phi = A.state[ST_PHI];
+    }
+    __syncthreads();
+
+    // ---- bound the source nodes whose footprint can reach the widened tile
+    {
+        const double SL = 0.02;   // cells; covers rounding of the FP32 push
+        const double EU = fabs(g.KU) * M, EV = fabs(g.KV) * M;
+        const double vd_min = g.vc_min + g.vr_min - EV, vd_max = g.vc_max + g.vr_max + EV;
+        const bool edge_lo = P0 == 0, edge_hi = P0 + TPe == np;
+        const int jlo = edge_lo ? 0 : max(0, (int)floor(P0 - R - vd_max - SL));
+        const int jhi = edge_hi ? np - 1 : min(np - 1, (int)ceil(P0 + TPe - 1 + R - vd_min + SL));
+        const double acc_lo = edge_lo ? -1e300 : (double)(P0 - R);
+        const double acc_hi = edge_hi ? 1e300 : (double)(P0 + TPe - 1 + R);
+        int my_ia = 0x7fffffff, my_ib = -0x7fffffff, my_ja = 0x7fffffff, my_jb = -0x7fffffff;
+        for (int j = jlo + tid; j <= jhi; j += blockDim.x) {
+            const RowBound rb = A.rowb[j];
+            long ia, ib;
+            double vcl = g.vc_min, vch = g.vc_max;
+            float smin = -1.f, smax = 1.f;
+            if (full) {
+                ia = 0;
+                ib = nx - 1;
+            } else {
+                ia = (long)floor(X0 - D - R - rb.u - EU - g.uc_max - SL);
+                ib = (long)ceil(X0 + TXe + D - 1 + R - rb.u + EU - g.uc_min + SL);
+                const long width = ib - ia + 1;
+                if (width < nx - 2 * kColBlock) {
+                    vcl = 1e300;
+                    vch = -1e300;
+                    const int start = imod((int)(ia % nx), nx);
+                    int seg_lo[2], seg_hi[2], nseg = 1;
+                    if (start + width <= nx) {
+                        seg_lo[0] = start;
+                        seg_hi[0] = (int)(start + width - 1);
+                    } else {
+                        seg_lo[0] = start;
+                        seg_hi[0] = nx - 1;
+                        seg_lo[1] = 0;
+                        seg_hi[1] = (int)(start + width - 1 - nx);
+                        nseg = 2;
+                    }
+                    for (int sg = 0; sg < nseg; ++sg)
+                        for (int b = seg_lo[sg] / kColBlock; b <= seg_hi[sg] / kColBlock; ++b) {
+                            vcl = fmin(vcl, A.vcb[2 * b]);
+                            vch = fmax(vch, A.vcb[2 * b + 1]);
+                        }
+                    if (EV > 0.0)
+                        sin_range_f(g.x0 + ia * g.hx - g.a_pad + rb.y + phi,
+                                    g.x0 + ib * g.hx + g.a_pad + rb.y + phi, smin, smax);
+                }
+            }
+            double tlo = 0.0, thi = 0.0;
+            if (EV > 0.0) {
+                const double k = g.KV * M;
+                tlo = fmin(k * smin, k * smax);
+                thi = fmax(k * smin, k * smax);
+            }
+            const double vlo = j + rb.v + vcl + tlo - SL;
+            const double vhi = j + rb.v + vch + thi + SL;
+            if (vhi > acc_lo && vlo < acc_hi) {
+                my_ia = min(my_ia, (int)ia);
+                my_ib = max(my_ib, (int)ib);
+                my_ja = min(my_ja, j);
+                my_jb = max(my_jb, j);
+            }
+        }
+        if (my_jb >= my_ja) {
+            atomicMin(&s_ia, my_ia);
+            atomicMax(&s_ib, my_ib);
+            atomicMin(&s_ja, my_ja);
+            atomicMax(&s_jb, my_jb);
+        }
+    }
+    __syncthreads();
+    const int ia = s_ia, ib = s_ib, ja = s_ja, jb = s_jb;
+    double lost = 0.0;
+
+    // ---- walk the source columns
+    if (jb >= ja) {
+        int wsrc = ib - ia + 1;
+        if (wsrc > nx) wsrc = nx;
+        const T alT = (T)al, beT = (T)be, KU = (T)g.KU, KV = (T)g.KV;
+        const T sixth = T(1) / T(6);
+        const T cp_inf = (T)A.piv[2 * kPivots], ib_inf = (T)A.piv[2 * kPivots + 1];
+        for (int cidx = tid; cidx < wsrc; cidx += blockDim.x) {
+            const int ic = ia + cidx;
+            const int im = imod(ic, nx);
+            const ColEntry<T> e = A.col[im];
+            ColC<T> cc;
+            cc.ui = e.ui;
+            cc.vi = e.vi;
+            cc.uf = e.uf;
+            cc.vf = e.vf;
+            // sine term: al sin(a + y) + be cos(a + y) = cy (al sa + be ca) + sy (al ca - be sa)
+            const T Pc = alT * e.sa + beT * e.ca, Qc = alT * e.ca - beT * e.sa;
+            cc.cu1 = KU * Pc;
+            cc.cu2 = KU * Qc;
+            cc.cv1 = KV * Pc;
+            cc.cv2 = KV * Qc;
+            const int colrel = ic - W.WX0;
+            const T *src = A.src + im;
+            Ring<T, N> rg;
+            rg.live = false;
+            rg.mref = 0;
+            rg.nb = 0;
+            rg.col_ok = false;
+#pragma unroll
+            for (int q = 0; q < N; ++q)
+#pragma unroll
+                for (int a = 0; a < N; ++a) rg.acc[q][a] = T(0);
+            T wx[N], wy[N];
+            if (!GAL) {
+                int j = ja;
+                for (; j + N - 1 <= jb; j += N) {
+#pragma unroll
+                    for (int u = 0; u < N; ++u) {
+                        const int jj = j + u;
+                        const T w = src[(size_t)jj * nx];
+                        int m, n;
+                        node_taps<T, BASIS, UTERM>(cc, A.row[jj], colrel, jj - W.WP0, w, m, n, wx, wy);
+                        ring_add<T, N, 1>(win, W, rg, m, n, wx, wy, lost, u);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < N; ++u) {
+                    const int jj = j + u;
+                    if (jj <= jb) {
+                        const T w = src[(size_t)jj * nx];
+                        int m, n;
+                        node_taps<T, BASIS, UTERM>(cc, A.row[jj], colrel, jj - W.WP0, w, m, n, wx, wy);
+                        ring_add<T, N, 1>(win, W, rg, m, n, wx, wy, lost, u);
+                    }
+                }
+                const int last_ph = (jb - ja) % N;
+#pragma unroll
+                for (int u = 0; u < N; ++u)
+                    if (u == last_ph) ring_final<T, N, 1>(win, W, rg, lost, u);
+            } else {
+                // forward sweep g_j = (s_j - g_{j-1} / 6) / beta_j into the ring yr
+                T yr[kChunk + kHalo];
+                const int r0 = max(0, ja - kHalo);
+                T gv = T(0);
+                for (int rr = r0; rr < ja; ++rr) {
+                    const T ibv = rr < kPivots ? (T)A.piv[2 * rr + 1] : ib_inf;
+                    gv = (src[(size_t)rr * nx] - sixth * gv) * ibv;
+                }
+#pragma unroll
+                for (int k = 0; k < kChunk + kHalo; ++k) {
+                    const int rr = ja + k;
+                    if (rr < np) {
+                        const T ibv = rr < kPivots ? (T)A.piv[2 * rr + 1] : ib_inf;
+                        gv = (src[(size_t)rr * nx] - sixth * gv) * ibv;
+                    }
+                    yr[k] = gv;
+                }
+                for (int c0 = ja; c0 <= jb; c0 += kChunk) {
+                    // back substitution w_j = g_j - c'_j w_{j+1}, from the look-ahead end
+                    const int top = min(c0 + kChunk + kHalo - 1, np - 1);
+                    T uv = T(0);
+#pragma unroll
+                    for (int k = kChunk + kHalo - 1; k >= kChunk; --k) {
+                        const int rr = c0 + k;
+                        if (rr <= top) {
+                            const T cpv = rr < kPivots ? (T)A.piv[2 * rr] : cp_inf;
+                            uv = yr[k] - cpv * uv;
+                        }
+                    }
+#pragma unroll
+                    for (int k = kChunk - 1; k >= 0; --k) {
+                        const int rr = c0 + k;
+                        if (rr <= top) {
+                            const T cpv = rr < kPivots ? (T)A.piv[2 * rr] : cp_inf;
+                            uv = yr[k] - cpv * uv;
+                            if (rr <= jb) {
+                                int m, n;
+                                node_taps<T, BASIS, UTERM>(cc, A.row[rr], colrel, rr - W.WP0, uv, m,
+                                                           n, wx, wy);
+                                ring_add<T, N, -1>(win, W, rg, m, n, wx, wy, lost, kChunk - 1 - k);
+                            }
+                        }
+                    }
+                    ring_final<T, N, -1>(win, W, rg, lost, kChunk - 1);
+#pragma unroll
+                    for (int k = 0; k < kHalo; ++k) yr[k] = yr[k + kChunk];
+#pragma unroll
+                    for (int k = kHalo; k < kChunk + kHalo; ++k) {
+                        const int rr = c0 + kChunk + k;
+                        if (rr < np) {
+                            const T ibv = rr < kPivots ? (T)A.piv[2 * rr + 1] : ib_inf;
+                            gv = (src[(size_t)rr * nx] - sixth * gv) * ibv;
+                        }
+                        yr[k] = gv;
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- window rows beyond the open momentum edge: lost weight of the own columns
+    for (int rr = 0; rr < W.WH; ++rr) {
+        const int grow = rr + W.WP0;
+        if (grow >= 0 && grow < np) continue;
+        const int c0 = full ? 0 : W.own_c0, c1 = full ? W.WW : W.own_c1;
+        for (int c = c0 + tid; c < c1; c += blockDim.x) lost += (double)win[rr * W.ws + c];
+    }
+    if (full) {
+        // fold the guard columns onto the period: [-G, 0) -> [nx - G, nx), [nx, nx + G) -> [0, G)
+        __syncthreads();
+        for (int k = tid; k < TPe * G; k += blockDim.x) {
+            const int rr = k / G + G, c = k - (k / G) * G;
+            T *row = win + (size_t)rr * W.ws;
+            row[nx + c] += row[c];
+            row[G + c] += row[G + nx + c];
+        }
+    }
+    __syncthreads();
+
+    // ---- store the tile (Galerkin: after the Lambda_x solve); FEL column sums
+    const bool want_part = A.fel_partials != 0;
+    bool bad = false;
+    double pw = 0.0, pc = 0.0, ps = 0.0;
+    if (GAL) {
+        T cs[kXMax];
+#pragma unroll
+        for (int k = 0; k < kXMax; ++k) cs[k] = T(0);
+        const int L = full ? nx : TXe + 2 * D;
+        int per = (L + 31) / 32, base = lane * per;   // same for every row (warps without rows too)
+        for (int rr = warp; rr < TPe; rr += nwarps) {
+            const T *row = win + (size_t)(rr + G) * W.ws + G;
+            T *dst_row = A.dst + (size_t)(P0 + rr) * nx + X0 - D;
+            T v[kXMax];
+            solve_row_x<T>(row, L, full, lane, v, per, base);
+            const T sig = want_part ? (T)A.sigma[P0 + rr] : T(0);
+#pragma unroll
+            for (int k = 0; k < kXMax; ++k) {
+                const int c = base + k;
+                if (k < per && c >= D && c < D + TXe) {
+                    dst_row[c] = v[k];
+                    bad |= !isfinite(v[k]);
+                    cs[k] += sig * v[k];
+                }
+            }
+        }
+        if (want_part) {
+            __syncthreads();   // the window is free now: per-warp column sums go there
+            T *slice = win + (size_t)warp * (L + 32);
+            for (int k = 0; k < kXMax; ++k)
+                if (k < per && base + k < L) slice[base + k] = cs[k];
+            __syncthreads();
+            for (int c = D + tid; c < D + TXe; c += blockDim.x) {
+                double sum = 0.0;
+                for (int w = 0; w < nwarps; ++w) sum += (double)win[(size_t)w * (L + 32) + c];
+                const double2 t = A.csx[X0 + c - D];
+                pw += sum;
+                pc += sum * t.x;
+                ps += sum * t.y;
+            }
+        }
+    } else {
+        for (int k = tid; k < TXe * TPe; k += blockDim.x) {
+            const int rr = k / TXe, c = k - rr * TXe;
+            const T v = win[(size_t)(rr + G) * W.ws + G + c];
+            A.dst[(size_t)(P0 + rr) * nx + X0 + c] = v;
+            bad |= !isfinite(v);
+        }
+        if (want_part)
+            for (int c = tid; c < TXe; c += blockDim.x) {
+                T s = T(0), comp = T(0);
+                for (int rr = 0; rr < TPe; ++rr) kahan(s, comp, win[(size_t)(rr + G) * W.ws + G + c]);
+                const double sum = (double)s - (double)comp;
+                const double2 t = A.csx[X0 + c];
+                pw += sum;
+                pc += sum * t.x;
+                ps += sum * t.y;
+            }
+    }
+    if (bad) atomicOr(A.err, ERRF_NONFINITE);
+
+    // ---- per-tile reductions in a fixed order
+    double vals[4] = {lost, pw, pc, ps};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        double v = vals[q];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) s_r4[q][warp] = v;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double t[4] = {0, 0, 0, 0};
+        for (int q = 0; q < 4; ++q)
+            for (int w = 0; w < nwarps; ++w) t[q] += s_r4[q][w];
+        A.tile_lost[tile] += t[0];
+        if (want_part) {
+            A.tile_part[3 * tile + 0] = t[1];
+            A.tile_part[3 * tile + 1] = t[2];
+            A.tile_part[3 * tile + 2] = t[3];
+        }
+    }
+}
+
+template <typename T>
+size_t fused_smem_bytes(int ws, int wh)
+{
+    return (size_t)ws * wh * sizeof(T);
+}
+
+template <typename T>
+cudaError_t launch_step_fused(const FusedArgs<T> &a, int threads, cudaStream_t s)
+{
+    const int wh = a.tp + 2 * a.G;
+    const size_t smem = fused_smem_bytes<T>(a.ws, wh);
+    const int grid = a.ntx * a.ntp;
+    const bool gal = a.g.basis == VP_BASIS_CUBIC_BSPLINE && a.g.projection == VP_PROJ_GALERKIN;
+    const bool uterm = a.g.kind == VP_PUSH_FEL_DKD;
+#define VP_LAUNCH_FUSED(B, GL, UT)                                                            \
+    do {                                                                                      \
+        auto k = step_fused_kernel<T, B, GL, UT>;                                             \
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
+                                             (int)smem);                                      \
+        if (e != cudaSuccess) return e;                                                       \
+        k<<<grid, threads, smem, s>>>(a);                                                     \
+    } while (0)
+    if (a.g.basis == VP_BASIS_TENT) {
+        if (uterm) VP_LAUNCH_FUSED(VP_BASIS_TENT, false, true);
+        else VP_LAUNCH_FUSED(VP_BASIS_TENT, false, false);
+    } else if (!gal) {
+        if (uterm) VP_LAUNCH_FUSED(VP_BASIS_CUBIC_BSPLINE, false, true);
+        else VP_LAUNCH_FUSED(VP_BASIS_CUBIC_BSPLINE, false, false);
+    } else {
+        if (uterm) VP_LAUNCH_FUSED(VP_BASIS_CUBIC_BSPLINE, true, true);
+        else VP_LAUNCH_FUSED(VP_BASIS_CUBIC_BSPLINE, true, false);
+    }
+#undef VP_LAUNCH_FUSED
+    return cudaGetLastError();
+}
+
+// s = Lambda_p w along columns (tridiag(1/6, 2/3, 1/6), zero beyond the open edges)
+template <typename T>
+__global__ void lambda_p_mul_kernel(const T *__restrict__ w, T *__restrict__ s, int nx, int np)
+{
+    const size_t n = (size_t)nx * np;
+    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int j = (int)(idx / nx);
+        const T c = w[idx];
+        const T lo = j > 0 ? w[idx - nx] : T(0);
+        const T hi = j + 1 < np ? w[idx + nx] : T(0);
+        s[idx] = (lo + hi) * (T(1) / T(6)) + c * (T(2) / T(3));
+    }
+}
+
+template <typename T>
+cudaError_t launch_lambda_p_mul(const T *w, T *s, int nx, int np, cudaStream_t st)
+{
+    size_t b = ((size_t)nx * np + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    lambda_p_mul_kernel<T><<<(int)b, 256, 0, st>>>(w, s, nx, np);
+    return cudaGetLastError();
+}
+
+template size_t fused_smem_bytes<float>(int, int);
+template size_t fused_smem_bytes<double>(int, int);
+template cudaError_t launch_step_fused<float>(const FusedArgs<float> &, int, cudaStream_t);
+template cudaError_t launch_step_fused<double>(const FusedArgs<double> &, int, cudaStream_t);
+template cudaError_t launch_lambda_p_mul<float>(const float *, float *, int, int, cudaStream_t);
+template cudaError_t launch_lambda_p_mul<double>(const double *, double *, int, int, cudaStream_t);
+
+}  // namespace vp

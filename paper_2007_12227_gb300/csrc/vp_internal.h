@@ -43,7 +43,8 @@ struct RowBound {
 // Device FEL / step state (doubles).
 enum {
     ST_A_RE = 0, ST_A_IM, ST_B_RE, ST_B_IM, ST_AH_RE, ST_AH_IM, ST_TAU, ST_STEP,
-    ST_HIST_HEAD, ST_NSTATE = 16
+    ST_M, ST_PHI,   // |A^{n+1/2}| and atan2(Re A, -Im A): amplitude and phase of the sine term
+    ST_NSTATE = 16
 };
 
 // Device error flag bits.
@@ -59,6 +60,7 @@ struct Geometry {
     double v_sign, omega, dt;
     double KU, KV;          // coefficients of the sine term
     double alpha0, beta0;   // sine-term weights for non-FEL pushers
+    double m0, phi0;        // hypot(alpha0, beta0), atan2(beta0, alpha0)
     double a_pad;           // bound on |a_i - x_i|
     double uc_min, uc_max;  // bounds of the column part of du
     double vc_min, vc_max;  // bounds of the column part of dv
@@ -83,6 +85,32 @@ struct StepArgs {
     int fel_partials;       // emit FEL partials from the step kernel
 };
 
+// One-pass step kernel (vp_fused.cu): see the description there.
+constexpr int kFusedMaxThreads = 320;
+
+template <typename T>
+struct FusedArgs {
+    const T *src;
+    T *dst;
+    const ColEntry<T> *col;
+    const RowEntry<T> *row;
+    const RowBound *rowb;
+    const double *vcb;
+    const double *state;
+    const double *piv;      // Thomas pivots of tridiag(1/6, 2/3, 1/6)
+    const double *sigma;    // column sums of Lambda_p^{-1} (FEL partial sums in Galerkin mode)
+    const double2 *csx;
+    double *tile_lost;
+    double *tile_part;
+    unsigned *err;
+    Geometry g;
+    int tx, tp, ntx, ntp;
+    int G;                  // guard band (cells) around the widened tile
+    int ws;                 // window row stride (elements)
+    int full_row;           // tiles span the whole x period (ntx == 1)
+    int fel_partials;
+};
+
 // ---- launch entry points (defined in the .cu files) -----------------------
 cudaError_t build_tables(const Geometry &g, int precision, void *col, void *row,
                          RowBound *rowb, double *ucol, double *vcol, double2 *csx, cudaStream_t s);
@@ -93,6 +121,15 @@ template <typename T>
 cudaError_t launch_step_scatter(const StepArgs<T> &a, double *lost_acc, cudaStream_t s);
 template <typename T>
 size_t tiled_smem_bytes(int tx, int tp);
+
+template <typename T>
+cudaError_t launch_step_fused(const FusedArgs<T> &a, int threads, cudaStream_t s);
+template <typename T>
+size_t fused_smem_bytes(int ws, int wh);
+constexpr int fused_halo(int precision) { return precision == VP_FP64 ? 28 : 14; }
+constexpr int kFusedMaxRow = 512; // longest window row one warp solves
+template <typename T>
+cudaError_t launch_lambda_p_mul(const T *w, T *s, int nx, int np, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_filter_x(const T *in, T *out, int nx, int np, unsigned *err, cudaStream_t s);

@@ -94,6 +94,8 @@ __global__ void fel_finalize_kernel(const double *__restrict__ part, int nparts,
         // A^0 already stored; A^{1/2} = A^0 + h/2 b^0
         state[ST_AH_RE] = state[ST_A_RE] + 0.5 * dt * b_re;
         state[ST_AH_IM] = state[ST_A_IM] + 0.5 * dt * b_im;
+        state[ST_M] = hypot(state[ST_AH_RE], state[ST_AH_IM]);
+        state[ST_PHI] = atan2(state[ST_AH_RE], -state[ST_AH_IM]);
         return;
     }
     const double are = state[ST_AH_RE] + 0.5 * dt * b_re;
@@ -102,6 +104,9 @@ __global__ void fel_finalize_kernel(const double *__restrict__ part, int nparts,
     state[ST_A_IM] = aim;
     state[ST_AH_RE] = are + 0.5 * dt * b_re;
     state[ST_AH_IM] = aim + 0.5 * dt * b_im;
+    // sine-term weights of the next push: alpha = -Im A, beta = Re A
+    state[ST_M] = hypot(state[ST_AH_RE], state[ST_AH_IM]);
+    state[ST_PHI] = atan2(state[ST_AH_RE], -state[ST_AH_IM]);
     const long step = (long)state[ST_STEP];
     if (hist && hist_cap > 0) {
         const long slot = step % hist_cap;

@@ -131,12 +131,13 @@ __global__ void __launch_bounds__(kThreads) step_tiled_kernel(const StepArgs<T> 
 
     for (int k = threadIdx.x; k < TX * TPh; k += blockDim.x) win[k] = T(0);
 
-    double al = g.alpha0, be = g.beta0;
+    double al = g.alpha0, be = g.beta0, M = g.m0, phi = g.phi0;
     if (g.kind == VP_PUSH_FEL_DKD) {
         al = -A.state[ST_AH_IM];
         be = A.state[ST_AH_RE];
+        M = A.state[ST_M];
+        phi = A.state[ST_PHI];
     }
-    const double M = hypot(al, be), phi = atan2(be, al);
     const double EU = fabs(g.KU) * M, EV = fabs(g.KV) * M;
     const T alT = (T)al, beT = (T)be, KUT = (T)g.KU, KVT = (T)g.KV;
     const double SL = 0.02;   // slack (cells) covering rounding of the FP32 push

@@ -22,7 +22,7 @@ VP_PUSH_LEAPFROG_KDK, VP_PUSH_EXACT_ROTATION, VP_PUSH_FEL_DKD = 0, 1, 2
 VP_POT_FREE, VP_POT_PENDULUM, VP_POT_HARMONIC = 0, 1, 2
 VP_FP32, VP_FP64 = 0, 1
 VP_PROJ_GALERKIN, VP_PROJ_LUMPED = 0, 1
-VP_KERNEL_AUTO, VP_KERNEL_TILED, VP_KERNEL_SCATTER = 0, 1, 2
+VP_KERNEL_AUTO, VP_KERNEL_TILED, VP_KERNEL_SCATTER, VP_KERNEL_FUSED = 0, 1, 2, 3
 
 
 class vp_grid(C.Structure):
@@ -63,6 +63,7 @@ _SIGNATURES = [
     ("vp_set_f", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_size_t]),
     ("vp_set_f_device", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_size_t]),
     ("vp_step", C.c_int, [C.c_void_p, C.c_int32]),
+    ("vp_step_profiled", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.c_int32]),
     ("vp_get_f", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_size_t]),
     ("vp_get_f_device", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_size_t]),
     ("vp_moments", C.c_int, [C.c_void_p, C.POINTER(vp_moments_t)]),
@@ -172,11 +173,20 @@ class Sim:
     def step(self, n=1):
         _check(lib().vp_step(self.h, int(n)), self.h)
 
+    def step_profiled(self, n=1):
+        """Advance n steps; returns summed device ms per phase (deposit, x solve, p solve, field)."""
+        ms = (C.c_double * 4)()
+        _check(lib().vp_step_profiled(self.h, int(n), ms, 4), self.h)
+        return list(ms)
+
     def get_f(self, dtype=np.float64):
         out = np.empty((self.np, self.nx), dtype=dtype)
         dt = VP_FP64 if out.dtype == np.float64 else VP_FP32
         _check(lib().vp_get_f(self.h, out.ctypes.data_as(C.c_void_p), dt, out.size), self.h)
         return out
+
+    def get_f_host_ptr(self, ptr: int, dtype: int):
+        _check(lib().vp_get_f(self.h, C.c_void_p(ptr), dtype, self.n), self.h)
 
     def get_f_device(self, out):
         import torch

@@ -91,7 +91,8 @@ def test_invalid_arguments_are_rejected_on_the_host(lib, bad):
         o.precision = 5
     elif bad == "period":
         g.x1 = 2.0                         # pendulum needs a 2 pi multiple period
-    elif bad == "tiles":
+    elif bad == "tiles":                   # the tiled kernel cannot hold a 4096^2 tile
+        o.kernel = V.VP_KERNEL_TILED
         o.tile_x = 4096
         o.tile_p = 4096
         g.nx, g.np = 8192, 8192
@@ -109,6 +110,18 @@ def test_create_rejects_missing_workspace(lib):
     h = C.c_void_p()
     st = lib.vp_create(C.byref(g), b, C.byref(pu), C.byref(o), None, 0, C.byref(h))
     assert st == V.VP_ERR_WORKSPACE and not h.value
+
+
+def test_planner_picks_the_fused_kernel_for_large_meshes(lib):
+    g, b, pu, o = _cfg(nx=4096, np_=2048)
+    o.kernel = V.VP_KERNEL_FUSED
+    assert V.vp_workspace_size(g, b, pu, o) > 0
+    g2, b2, pu2, o2 = _cfg(nx=520, np_=64)       # window (480 + halo + guard) wider than the mesh
+    o2.kernel = V.VP_KERNEL_FUSED
+    o2.tile_x = 480
+    n = C.c_size_t()
+    st = lib.vp_workspace_size(C.byref(g2), b2, C.byref(pu2), C.byref(o2), C.byref(n))
+    assert st == V.VP_ERR_UNSUPPORTED
 
 
 def test_status_strings(lib):

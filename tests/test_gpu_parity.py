@@ -94,10 +94,11 @@ def test_pendulum_128_fp64_tent_full_run(kernel):
                                         (I.BASIS_CUBIC, I.PROJ_GALERKIN),
                                         (I.BASIS_CUBIC, I.PROJ_LUMPED)])
 @pytest.mark.parametrize("shape,tile", [((200, 150), (64, 64)), ((96, 97), (32, 32)),
-                                        ((37, 23), (0, 0))])
-def test_pendulum_fp64_ragged_tiles(basis, proj, shape, tile):
+                                        ((37, 23), (0, 0)), ((300, 130), (96, 48))])
+@pytest.mark.parametrize("kernel", [V.VP_KERNEL_TILED, V.VP_KERNEL_FUSED])
+def test_pendulum_fp64_ragged_tiles(basis, proj, shape, tile, kernel):
     wl = pend(shape[0], shape[1], basis, I.FP64, dt=0.07, pc=0.8, s=0.5)
-    got, st, _, _, _ = run_pair(wl, 15, kernel=V.VP_KERNEL_TILED, tile=tile, projection=proj)
+    got, st, _, _, _ = run_pair(wl, 15, kernel=kernel, tile=tile, projection=proj)
     check(got, st.w, I.FP64)
 
 
@@ -130,7 +131,7 @@ def test_large_displacement_wraps_many_periods():
     g = I.Grid(16, 12, -PI, PI, -20.0, 20.0)
     pu = I.Pusher(I.PUSH_KDK, I.POT_PENDULUM, 1.0, 1.0, 0.9)
     wl = I.Workload("t", g, pu, I.BASIS_CUBIC, I.FP64, 0, "gaussian", dict(xc=0.0, pc=0.0, sx=1.0, sp=9.0))
-    for kernel in (V.VP_KERNEL_TILED, V.VP_KERNEL_SCATTER):
+    for kernel in (V.VP_KERNEL_TILED, V.VP_KERNEL_SCATTER, V.VP_KERNEL_FUSED):
         got, st, _, _, _ = run_pair(wl, 4, kernel=kernel)
         check(got, st.w, I.FP64)
 
@@ -138,7 +139,7 @@ def test_large_displacement_wraps_many_periods():
 # ----------------------------------------------------------------------------- FEL, FP64
 @pytest.mark.parametrize("basis,proj", [(I.BASIS_CUBIC, I.PROJ_GALERKIN), (I.BASIS_TENT, I.PROJ_GALERKIN),
                                         (I.BASIS_CUBIC, I.PROJ_LUMPED)])
-@pytest.mark.parametrize("kernel", [V.VP_KERNEL_TILED, V.VP_KERNEL_SCATTER])
+@pytest.mark.parametrize("kernel", [V.VP_KERNEL_TILED, V.VP_KERNEL_SCATTER, V.VP_KERNEL_FUSED])
 def test_fel_fp64_field_history(basis, proj, kernel):
     wl = fel(64, 96, I.FP64, dt=0.05, a0=0.05, sp=0.1, pr=(-1.0, 1.0), basis=basis)
     got, st, mom, hist, ohist = run_pair(wl, 40, kernel=kernel, projection=proj)
@@ -158,8 +159,8 @@ def test_pendulum_fp32_cubic_reduced_grid():
 
 
 def test_fel_fp32_cubic_reduced_grid():
-    """The 4096 x 2048 FEL workload's physics on 256 x 128, 300 steps (tau = 3)."""
-    wl = fel(256, 128, I.FP32)
+    """The 4096 x 2048 FEL workload's physics (sigma_p 0.05 resolved by ~8 cells) on 256 x 256."""
+    wl = fel(256, 256, I.FP32, pr=(-0.8, 0.8))
     got, st, _, hist, ohist = run_pair(wl, 300)
     check(got, st.w, I.FP32)
     amp = np.hypot(ohist[:, 0], ohist[:, 1])
@@ -167,12 +168,44 @@ def test_fel_fp32_cubic_reduced_grid():
     assert rel <= 1e-5, f"|A| rel err {rel:.2e}"
 
 
-@pytest.mark.parametrize("kernel", [V.VP_KERNEL_TILED, V.VP_KERNEL_SCATTER])
+@pytest.mark.parametrize("kernel", [V.VP_KERNEL_TILED, V.VP_KERNEL_SCATTER, V.VP_KERNEL_FUSED])
 def test_fp32_tent_and_lumped(kernel):
     for basis, proj in ((I.BASIS_TENT, I.PROJ_GALERKIN), (I.BASIS_CUBIC, I.PROJ_LUMPED)):
         wl = pend(300, 260, basis, I.FP32, dt=0.03, pr=(-4.0, 4.0), pc=0.5, s=0.5)
         got, st, _, _, _ = run_pair(wl, 30, kernel=kernel, projection=proj)
         check(got, st.w, I.FP32)
+
+
+@pytest.mark.parametrize("tile", [(224, 64), (480, 32), (96, 128)])
+def test_fused_fp32_galerkin_windowed_tiles(tile):
+    """Fused one-pass kernel, windowed (not whole-row) tiles, ragged last tiles."""
+    wl = pend(1100, 700, I.BASIS_CUBIC, I.FP32, dt=0.02, pr=(-4.0, 4.0), pc=0.5, s=0.4)
+    got, st, mom, _, _ = run_pair(wl, 25, kernel=V.VP_KERNEL_FUSED, tile=tile)
+    check(got, st.w, I.FP32)
+    om = st.moments()
+    assert abs(mom["mass"] - om["mass"]) <= 1e-6 * om["mass"]
+
+
+def test_fused_fp32_fel_windowed():
+    wl = fel(1024, 512, I.FP32, pr=(-0.8, 0.8), a0=0.05)
+    got, st, _, hist, ohist = run_pair(wl, 60, kernel=V.VP_KERNEL_FUSED)
+    check(got, st.w, I.FP32)
+    amp = np.hypot(ohist[:, 0], ohist[:, 1])
+    assert np.max(np.abs(np.hypot(hist[:, 0], hist[:, 1]) - amp) / amp) <= 1e-5
+
+
+def test_fused_matches_tiled_on_gpu():
+    """Both GPU step kernels compute the same update (FP64, several steps)."""
+    wl = pend(600, 400, I.BASIS_CUBIC, I.FP64, dt=0.03, pr=(-4.0, 4.0), pc=0.5, s=0.4)
+    f0 = I.make_f0(wl)
+    outs = []
+    for kernel in (V.VP_KERNEL_TILED, V.VP_KERNEL_FUSED):
+        sim = V.Sim(wl.grid, wl.basis, wl.pusher, precision=I.FP64, kernel=kernel)
+        sim.set_f(f0)
+        sim.step(10)
+        outs.append(sim.get_f())
+        sim.close()
+    assert rel_linf(outs[1], outs[0]) <= 1e-13
 
 
 # ------------------------------------------------------------------------------ edge cases
