@@ -38,7 +38,7 @@ struct Plan {
     bool galerkin, fel;
     // fused kernel: guard band, window stride, threads per CTA, whole-period tiles;
     // state_s: the stored state is s = Lambda_x^{-1} r instead of the weights w
-    int G, ws, threads;
+    int G, Gp, ws, threads;
     bool full_row, state_s;
     Layout L;
 };
@@ -132,7 +132,8 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     const size_t sz = opts->precision == VP_FP64 ? 8 : 4;
     const bool wide_rotation = pu->kind == VP_PUSH_EXACT_ROTATION && fabs(pu->omega * h) >= 0.5 * M_PI;
     int kernel = opts->kernel;
-    P->G = 8;
+    P->G = 6;
+    P->Gp = 8;
     P->full_row = false;
     P->ws = 0;
     P->threads = 0;
@@ -140,7 +141,7 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     if (kernel == VP_KERNEL_AUTO || kernel == VP_KERNEL_FUSED) {
         const int halo = P->galerkin ? fused_halo(opts->precision) : 0;
         const int R = basis == VP_BASIS_TENT ? 1 : 2;
-        const int G = P->G;
+        const int G = P->G, Gp = P->Gp;
         ftx = opts->tile_x ? opts->tile_x : (opts->precision == VP_FP64 ? 128 : 224);
         ftp = opts->tile_p ? opts->tile_p : 64;
         bool full = false;
@@ -152,15 +153,21 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
         ftp = std::min(ftp, grid->np);
         const int WW = full ? grid->nx + 2 * G : ftx + 2 * halo + 2 * G;
         const int ws = (WW + 31) / 32 * 32 + 1;
-        while ((size_t)ws * (ftp + 2 * G) * sz > 110 * 1024 && ftp > 8) ftp /= 2;
-        const size_t smem = (size_t)ws * (ftp + 2 * G) * sz;
+        const int wsrc = (full ? grid->nx : ftx + 2 * halo) + 2 * R + 8;
+        const int threads = std::min(kFusedMaxThreads, (wsrc + 31) / 32 * 32);
+        // two CTAs per SM when the window allows it
+        auto smem_of = [&](int tp_) {
+            return sz == 8 ? fused_smem_bytes<double>(ws, tp_ + 2 * Gp, threads)
+                           : fused_smem_bytes<float>(ws, tp_ + 2 * Gp, threads);
+        };
+        while (smem_of(ftp) > 112 * 1024 && ftp > 8) ftp /= 2;
+        const size_t smem = smem_of(ftp);
         const bool ok = !wide_rotation && smem <= kMaxSmem && (full || WW < grid->nx) && ftx >= 1;
         if (ok) {
             kernel = VP_KERNEL_FUSED;
             P->full_row = full;
             P->ws = ws;
-            const int wsrc = (full ? grid->nx : ftx + 2 * halo) + 2 * R + 8;
-            P->threads = std::min(kFusedMaxThreads, (wsrc + 31) / 32 * 32);
+            P->threads = threads;
         } else if (kernel == VP_KERNEL_FUSED) {
             return fail(msg, VP_ERR_UNSUPPORTED,
                         "the fused kernel needs a mesh wider than its window (nx = %d)", grid->nx);
@@ -318,6 +325,7 @@ FusedArgs<T> fused_args(vp_sim *s, const void *src, void *dst)
     a.ntx = P.ntx;
     a.ntp = P.ntp;
     a.G = P.G;
+    a.Gp = P.Gp;
     a.ws = P.ws;
     a.full_row = P.full_row ? 1 : 0;
     a.fel_partials = P.fel ? 1 : 0;

@@ -14,10 +14,11 @@
 // band G. It bounds the source nodes whose pushed B3 footprint reaches the
 // widened tile and gives each thread one source column. The thread walks the
 // column:
-//   * Galerkin: the p solve is the Thomas sweep of tridiag(1/6, 2/3, 1/6)
-//     (exact pivots near row 0): the forward sweep runs into a register ring,
-//     the back substitution runs over chunks of kChunk rows with kHalo rows
-//     of look-ahead (truncation |z|^kHalo, z = sqrt(3) - 2);
+//   * Galerkin: the p solve is the Thomas algorithm for tridiag(1/6, 2/3, 1/6)
+//     (exact pivots near row 0), walked downwards in chunks of kC rows: the
+//     forward sweep of a chunk starts kHalo rows below it (truncation
+//     |z|^kHalo, z = sqrt(3) - 2) and is kept in a shared-memory column buffer;
+//     the back substitution carries on from the chunk above;
 //   * every node is pushed (displacement tables, vp_internal.h) and its N x N
 //     taps accumulate in an N x N register ring that follows the node's base
 //     row; when the ring moves one row, the row that leaves it is added to the
@@ -39,8 +40,18 @@ template <typename T>
 struct Halo {
     static constexpr int value = sizeof(T) == 4 ? 14 : 28;
 };
-constexpr int kChunk = 16;          // rows per backward sweep
+constexpr int kC = 16;              // rows per chunk of the p solve (multiple of 4)
+// rows of the per-thread column buffer: one chunk, or the look-ahead above the top row
+template <typename T>
+struct GRows {
+    static constexpr int value = kC > Halo<T>::value ? kC : Halo<T>::value;
+};
 constexpr int kXMax = kFusedMaxRow / 32;
+
+template <int U>
+struct IC {
+    static constexpr int value = U;
+};
 
 template <typename T, int BASIS>
 struct FTaps;
@@ -129,7 +140,7 @@ __device__ __forceinline__ void kahan(T &sum, T &comp, T v)
 
 template <typename T, int N>
 struct Ring {
-    T acc[N][N];
+    T acc[N][N];  // [slot][column]
     int mref;     // window column of tap a = 0
     int nb;       // window row of tap b = 0 of the last node
     bool col_ok;  // all N columns inside the window
@@ -144,6 +155,31 @@ struct WinGeom {
     bool full;           // the tile spans the whole period
 };
 
+// One cell outside the fast window range: wrap (whole-period tiles), add, or count
+// as lost (rows beyond the open momentum edge, own columns). Returns the lost weight.
+template <typename T>
+__device__ __noinline__ double flush_cell_slow(T *win, const WinGeom W, T v, int c, int row)
+{
+    if (W.full && (c < 0 || c >= W.WW)) c = W.G + imod(c - W.G, W.nx);
+    const int grow = row + W.WP0;
+    const bool outside = grow < 0 || grow >= W.np;
+    if (c >= 0 && c < W.WW) {
+        if (row >= 0 && row < W.WH) {
+            atomicAdd(win + row * W.ws + c, v);
+            return 0.0;
+        }
+        if (outside && (W.full || (c >= W.own_c0 && c < W.own_c1))) return (double)v;
+    }
+    return 0.0;
+}
+
+template <typename T>
+__device__ __forceinline__ void flush_cell(T *win, const WinGeom &W, T v, int c, int row, double &lost)
+{
+    if (row >= 0 && row < W.WH && c >= 0 && c < W.WW) atomicAdd(win + row * W.ws + c, v);
+    else lost += flush_cell_slow<T>(win, W, v, c, row);
+}
+
 template <typename T, int N>
 __device__ __forceinline__ void flush_row(T *win, const WinGeom &W, const T *acc, int mref,
                                           bool col_ok, int row, double &lost)
@@ -152,77 +188,129 @@ __device__ __forceinline__ void flush_row(T *win, const WinGeom &W, const T *acc
         T *p = win + row * W.ws + mref;
 #pragma unroll
         for (int a = 0; a < N; ++a) atomicAdd(p + a, acc[a]);
-        return;
-    }
-    const int grow = row + W.WP0;
-    const bool outside = grow < 0 || grow >= W.np;
-    const bool rin = row >= 0 && row < W.WH;
+    } else {
 #pragma unroll
-    for (int a = 0; a < N; ++a) {
-        int c = mref + a;
-        if (W.full && (c < 0 || c >= W.WW)) c = W.G + imod(c - W.G, W.nx);   // wrap onto the period
-        if (c >= 0 && c < W.WW) {
-            if (rin) atomicAdd(win + row * W.ws + c, acc[a]);
-            else if (outside && (W.full || (c >= W.own_c0 && c < W.own_c1))) lost += (double)acc[a];
-        } else if (outside && W.full) {
-            lost += (double)acc[a];
-        }
+        for (int a = 0; a < N; ++a) lost += flush_cell_slow<T>(win, W, acc[a], mref + a, row);
     }
+}
+
+// slot of tap row b at phase ph: (b + ph) % N ascending, (b - ph) % N descending
+template <int N, int DIR, int PH>
+__device__ __forceinline__ constexpr int slot(int b)
+{
+    return DIR > 0 ? (b + PH) % N : (b - PH % N + N) % N;
 }
 
 // Add one node (weights wx, wy; base window column m, row n) at static phase PH.
-// DIR = +1: base rows ascend between consecutive calls; DIR = -1: they descend.
-// Slot of tap row b: (b + PH) % N ascending, (b - PH) % N descending.
-template <typename T, int N, int DIR>
+// DIR = +1: base rows ascend between consecutive nodes; DIR = -1: they descend.
+template <typename T, int N, int DIR, int PH>
 __device__ __forceinline__ void ring_add(T *win, const WinGeom &W, Ring<T, N> &rg, int m, int n,
-                                         const T *wx, const T *wy, double &lost, const int PH)
+                                         const T *wx, const T *wy, double &lost)
 {
-    const int PHN = PH % N;
-    const int PP = (PH + N - 1) % N;   // phase of the previous node
-    if (!(rg.live && m == rg.mref && n == rg.nb + DIR)) {
-        if (rg.live) {
+    constexpr int PP = (PH + N - 1) % N;   // phase of the previous node
+    const bool step_ok = rg.live && n == rg.nb + DIR;
+    if (step_ok && (m == rg.mref + 1 || m == rg.mref - 1)) {
+        // the base column moved by one: flush the column that leaves, shift the rest
+        const bool left = m > rg.mref;
 #pragma unroll
-            for (int b = 0; b < N; ++b) {
-                const int q = DIR > 0 ? (b + PP) % N : (b - PP + N) % N;
-                flush_row<T, N>(win, W, rg.acc[q], rg.mref, rg.col_ok, rg.nb + b, lost);
+        for (int b = 0; b < N; ++b) {
+            const int q = slot<N, DIR, PP>(b);
+            if (left) {
+                flush_cell<T>(win, W, rg.acc[q][0], rg.mref, rg.nb + b, lost);
+#pragma unroll
+                for (int a = 0; a < N - 1; ++a) rg.acc[q][a] = rg.acc[q][a + 1];
+                rg.acc[q][N - 1] = T(0);
+            } else {
+                flush_cell<T>(win, W, rg.acc[q][N - 1], rg.mref + N - 1, rg.nb + b, lost);
+#pragma unroll
+                for (int a = N - 1; a > 0; --a) rg.acc[q][a] = rg.acc[q][a - 1];
+                rg.acc[q][0] = T(0);
             }
         }
-#pragma unroll
-        for (int q = 0; q < N; ++q)
-#pragma unroll
-            for (int a = 0; a < N; ++a) rg.acc[q][a] = T(0);
         rg.mref = m;
-        rg.col_ok = m >= 0 && m + N <= W.WW;
-        rg.live = true;
-    } else {
-        // the ring moves one row: the row leaving it is complete
-        const int q = DIR > 0 ? (PHN + N - 1) % N : (N - PHN) % N;
-        const int row = DIR > 0 ? rg.nb : rg.nb + N - 1;
-        flush_row<T, N>(win, W, rg.acc[q], rg.mref, rg.col_ok, row, lost);
-#pragma unroll
-        for (int a = 0; a < N; ++a) rg.acc[q][a] = T(0);
+        rg.col_ok = (unsigned)m <= (unsigned)(W.WW - N);   // overflow-safe for any m
     }
-    rg.nb = n;
+    if (step_ok && m == rg.mref) {
+        // the ring moves one row: flush the row leaving it, the entering row starts fresh
+        const int bl = DIR > 0 ? 0 : N - 1;           // leaving row, previous node's tap index
+        const int ql = slot<N, DIR, PP>(bl);
+        flush_row<T, N>(win, W, rg.acc[ql], rg.mref, rg.col_ok, rg.nb + bl, lost);
+        const int be = DIR > 0 ? N - 1 : 0;           // entering row, this node's tap index
+#pragma unroll
+        for (int b = 0; b < N; ++b) {
+            const int q = slot<N, DIR, PH>(b);
+            if (b == be) {
+#pragma unroll
+                for (int a = 0; a < N; ++a) rg.acc[q][a] = wy[b] * wx[a];
+            } else {
+#pragma unroll
+                for (int a = 0; a < N; ++a) rg.acc[q][a] += wy[b] * wx[a];
+            }
+        }
+        rg.nb = n;
+        return;
+    }
+    // anything else (first node, a jump): flush the whole ring and restart
+    if (rg.live) {
+#pragma unroll
+        for (int b = 0; b < N; ++b) {
+            const int q = slot<N, DIR, PP>(b);
+            flush_row<T, N>(win, W, rg.acc[q], rg.mref, rg.col_ok, rg.nb + b, lost);
+        }
+    }
 #pragma unroll
     for (int b = 0; b < N; ++b) {
-        const int q = DIR > 0 ? (b + PHN) % N : (b - PHN + N) % N;
+        const int q = slot<N, DIR, PH>(b);
 #pragma unroll
-        for (int a = 0; a < N; ++a) rg.acc[q][a] += wy[b] * wx[a];
+        for (int a = 0; a < N; ++a) rg.acc[q][a] = wy[b] * wx[a];
     }
+    rg.mref = m;
+    rg.nb = n;
+    rg.col_ok = (unsigned)m <= (unsigned)(W.WW - N);   // overflow-safe for any m
+    rg.live = true;
 }
 
-template <typename T, int N, int DIR>
-__device__ __forceinline__ void ring_final(T *win, const WinGeom &W, Ring<T, N> &rg, double &lost,
-                                           const int PH)
+template <typename T, int N, int DIR, int PH>
+__device__ __forceinline__ void ring_final(T *win, const WinGeom &W, Ring<T, N> &rg, double &lost)
 {
     if (!rg.live) return;
-    const int PHN = PH % N;
 #pragma unroll
     for (int b = 0; b < N; ++b) {
-        const int q = DIR > 0 ? (b + PHN) % N : (b - PHN + N) % N;
+        const int q = slot<N, DIR, PH>(b);
         flush_row<T, N>(win, W, rg.acc[q], rg.mref, rg.col_ok, rg.nb + b, lost);
     }
     rg.live = false;
+}
+
+// floor of x as a value and as an int without float-to-int conversion instructions:
+// adding 1.5 * 2^(mantissa bits) rounds to an integer held in the low mantissa bits
+// (valid for |x| < 2^22 in FP32, 2^51 in FP64); one compare turns rounding into floor.
+__device__ __forceinline__ void floor_split(float x, float &fl, int &i)
+{
+    const float magic = 12582912.0f;   // 1.5 * 2^23
+    const float t = x + magic;
+    float r = t - magic;
+    int k = __float_as_int(t) - 0x4B400000;
+    if (r > x) {
+        r -= 1.0f;
+        k -= 1;
+    }
+    fl = r;
+    i = k;
+}
+
+__device__ __forceinline__ void floor_split(double x, double &fl, int &i)
+{
+    const double magic = 6755399441055744.0;   // 1.5 * 2^52
+    const double t = x + magic;
+    double r = t - magic;
+    int k = (int)(__double_as_longlong(t) - 0x4338000000000000LL);
+    if (r > x) {
+        r -= 1.0;
+        k -= 1;
+    }
+    fl = r;
+    i = k;
 }
 
 template <typename T>
@@ -239,9 +327,12 @@ __device__ __forceinline__ void node_taps(const ColC<T> &c, const RowEntry<T> &r
     T fu = c.uf + r.uf;
     if (UTERM) fu += c.cu1 * r.cy + c.cu2 * r.sy;
     const T fv = (c.vf + r.vf) + c.cv1 * r.cy + c.cv2 * r.sy;
-    const T flu = floor(fu), flv = floor(fv);
-    m = colrel + c.ui + r.ui + (int)flu + TP::LO;
-    n = rowrel + c.vi + r.vi + (int)flv + TP::LO;
+    T flu, flv;
+    int iu, iv;
+    floor_split(fu, flu, iu);
+    floor_split(fv, flv, iv);
+    m = colrel + c.ui + r.ui + iu + TP::LO;
+    n = rowrel + c.vi + r.vi + iv + TP::LO;
     TP::weights(fu - flu, wx);
     TP::weights(fv - flv, wy);
 #pragma unroll
@@ -359,8 +450,11 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const F
     constexpr int R = (BASIS == VP_BASIS_TENT) ? 1 : 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *win = reinterpret_cast<T *>(smem_raw);
+    T *gcol = win + (size_t)A.ws * (A.tp + 2 * A.Gp);   // [GRows][blockDim] column buffer (Galerkin)
     __shared__ int s_ia, s_ib, s_ja, s_jb;
     __shared__ double s_r4[4][kFusedMaxThreads / 32];
+    // Thomas pivots of tridiag(1/6, 2/3, 1/6) in T: entry kPivots holds the limit
+    __shared__ T piv_cp[kPivots + 1], piv_ib[kPivots + 1];
 
     const Geometry &g = A.g;
     const int nx = g.nx, np = g.np;
@@ -371,13 +465,13 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const F
     const bool full = A.full_row != 0;
     constexpr int kHalo = Halo<T>::value;
     const int D = (GAL && !full) ? kHalo : 0;
-    const int G = A.G;
+    const int G = A.G, Gp = A.Gp;   // guard bands: columns, rows
     WinGeom W;
     W.WW = full ? nx + 2 * G : TXe + 2 * D + 2 * G;
-    W.WH = TPe + 2 * G;
+    W.WH = TPe + 2 * Gp;
     W.ws = A.ws;
     W.WX0 = X0 - D - G;
-    W.WP0 = P0 - G;
+    W.WP0 = P0 - Gp;
     W.own_c0 = G + D;
     W.own_c1 = G + D + TXe;
     W.np = np;
@@ -387,6 +481,10 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const F
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
 
     for (int k = tid; k < W.WH * W.ws; k += blockDim.x) win[k] = T(0);
+    for (int k = tid; k <= kPivots; k += blockDim.x) {
+        piv_cp[k] = (T)A.piv[2 * k];
+        piv_ib[k] = (T)A.piv[2 * k + 1];
+    }
     if (tid == 0) {
         s_ia = 0x7fffffff;
         s_ib = -0x7fffffff;
@@ -482,7 +580,6 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const F
         if (wsrc > nx) wsrc = nx;
         const T alT = (T)al, beT = (T)be, KU = (T)g.KU, KV = (T)g.KV;
         const T sixth = T(1) / T(6);
-        const T cp_inf = (T)A.piv[2 * kPivots], ib_inf = (T)A.piv[2 * kPivots + 1];
         for (int cidx = tid; cidx < wsrc; cidx += blockDim.x) {
             const int ic = ia + cidx;
             const int im = imod(ic, nx);
@@ -511,87 +608,92 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const F
                 for (int a = 0; a < N; ++a) rg.acc[q][a] = T(0);
             T wx[N], wy[N];
             if (!GAL) {
-                int j = ja;
-                for (; j + N - 1 <= jb; j += N) {
-#pragma unroll
-                    for (int u = 0; u < N; ++u) {
-                        const int jj = j + u;
-                        const T w = src[(size_t)jj * nx];
-                        int m, n;
-                        node_taps<T, BASIS, UTERM>(cc, A.row[jj], colrel, jj - W.WP0, w, m, n, wx, wy);
-                        ring_add<T, N, 1>(win, W, rg, m, n, wx, wy, lost, u);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < N; ++u) {
-                    const int jj = j + u;
+                // ascending walk in groups of N rows; each phase is a template constant
+                auto row_step = [&](auto ph, int jj) {
+                    constexpr int u = decltype(ph)::value;
                     if (jj <= jb) {
                         const T w = src[(size_t)jj * nx];
                         int m, n;
                         node_taps<T, BASIS, UTERM>(cc, A.row[jj], colrel, jj - W.WP0, w, m, n, wx, wy);
-                        ring_add<T, N, 1>(win, W, rg, m, n, wx, wy, lost, u);
+                        ring_add<T, N, 1, u>(win, W, rg, m, n, wx, wy, lost);
+                    }
+                };
+                for (int j = ja; j <= jb; j += N) {
+                    row_step(IC<0>{}, j);
+                    row_step(IC<1>{}, j + 1);
+                    if constexpr (N > 2) {
+                        row_step(IC<2>{}, j + 2);
+                        row_step(IC<3>{}, j + 3);
                     }
                 }
                 const int last_ph = (jb - ja) % N;
-#pragma unroll
-                for (int u = 0; u < N; ++u)
-                    if (u == last_ph) ring_final<T, N, 1>(win, W, rg, lost, u);
+                if (last_ph == 0) ring_final<T, N, 1, 0>(win, W, rg, lost);
+                if (last_ph == 1) ring_final<T, N, 1, 1>(win, W, rg, lost);
+                if constexpr (N > 2) {
+                    if (last_ph == 2) ring_final<T, N, 1, 2 % N>(win, W, rg, lost);
+                    if (last_ph == 3) ring_final<T, N, 1, 3 % N>(win, W, rg, lost);
+                }
             } else {
-                // forward sweep g_j = (s_j - g_{j-1} / 6) / beta_j into the ring yr
-                T yr[kChunk + kHalo];
-                const int r0 = max(0, ja - kHalo);
-                T gv = T(0);
-                for (int rr = r0; rr < ja; ++rr) {
-                    const T ibv = rr < kPivots ? (T)A.piv[2 * rr + 1] : ib_inf;
-                    gv = (src[(size_t)rr * nx] - sixth * gv) * ibv;
+                // Lambda_p^{-1} s by the Thomas algorithm, walked downwards in chunks of
+                // kC rows: forward sweep g_j = (s_j - g_{j-1}/6) / beta_j from kHalo rows
+                // below the chunk (or from row 0), kept in the column buffer gcol;
+                // back substitution w_j = g_j - c'_j w_{j+1} continues from the chunk above.
+                T *gc = gcol + tid;
+                const int nth = blockDim.x;
+                T uv = T(0);
+                {
+                    // look-ahead above jb (exact when it reaches the last row)
+                    const int top = min(np - 1, jb + kHalo);
+                    if (top > jb) {
+                        int rr = max(0, jb + 1 - kHalo);
+                        T gv = T(0);
+#pragma unroll 4
+                        for (; rr <= jb; ++rr)
+                            gv = (src[(size_t)rr * nx] - sixth * gv) * piv_ib[min(rr, kPivots)];
+#pragma unroll 4
+                        for (; rr <= top; ++rr) {
+                            gv = (src[(size_t)rr * nx] - sixth * gv) * piv_ib[min(rr, kPivots)];
+                            gc[(rr - jb - 1) * nth] = gv;
+                        }
+                        for (rr = top; rr > jb; --rr) uv = gc[(rr - jb - 1) * nth] - piv_cp[min(rr, kPivots)] * uv;
+                    }
                 }
-#pragma unroll
-                for (int k = 0; k < kChunk + kHalo; ++k) {
-                    const int rr = ja + k;
-                    if (rr < np) {
-                        const T ibv = rr < kPivots ? (T)A.piv[2 * rr + 1] : ib_inf;
-                        gv = (src[(size_t)rr * nx] - sixth * gv) * ibv;
+                auto row_step = [&](auto ph, int r, int c_lo) {
+                    constexpr int u = decltype(ph)::value;
+                    if (r >= c_lo) {
+                        uv = gc[(r - c_lo) * nth] - piv_cp[min(r, kPivots)] * uv;
+                        int m, n;
+                        node_taps<T, BASIS, UTERM>(cc, A.row[r], colrel, r - W.WP0, uv, m, n, wx, wy);
+                        ring_add<T, N, -1, u>(win, W, rg, m, n, wx, wy, lost);
                     }
-                    yr[k] = gv;
+                };
+                for (int c_hi = jb; c_hi >= ja; c_hi -= kC) {
+                    const int c_lo = max(ja, c_hi - kC + 1);
+                    int rr = max(0, c_lo - kHalo);
+                    T gv = T(0);
+#pragma unroll 4
+                    for (; rr < c_lo; ++rr)
+                        gv = (src[(size_t)rr * nx] - sixth * gv) * piv_ib[min(rr, kPivots)];
+#pragma unroll 4
+                    for (; rr <= c_hi; ++rr) {
+                        gv = (src[(size_t)rr * nx] - sixth * gv) * piv_ib[min(rr, kPivots)];
+                        gc[(rr - c_lo) * nth] = gv;
+                    }
+                    for (int r4 = c_hi; r4 >= c_lo; r4 -= N) {
+                        row_step(IC<0>{}, r4, c_lo);
+                        row_step(IC<1>{}, r4 - 1, c_lo);
+                        if constexpr (N > 2) {
+                            row_step(IC<2>{}, r4 - 2, c_lo);
+                            row_step(IC<3>{}, r4 - 3, c_lo);
+                        }
+                    }
                 }
-                for (int c0 = ja; c0 <= jb; c0 += kChunk) {
-                    // back substitution w_j = g_j - c'_j w_{j+1}, from the look-ahead end
-                    const int top = min(c0 + kChunk + kHalo - 1, np - 1);
-                    T uv = T(0);
-#pragma unroll
-                    for (int k = kChunk + kHalo - 1; k >= kChunk; --k) {
-                        const int rr = c0 + k;
-                        if (rr <= top) {
-                            const T cpv = rr < kPivots ? (T)A.piv[2 * rr] : cp_inf;
-                            uv = yr[k] - cpv * uv;
-                        }
-                    }
-#pragma unroll
-                    for (int k = kChunk - 1; k >= 0; --k) {
-                        const int rr = c0 + k;
-                        if (rr <= top) {
-                            const T cpv = rr < kPivots ? (T)A.piv[2 * rr] : cp_inf;
-                            uv = yr[k] - cpv * uv;
-                            if (rr <= jb) {
-                                int m, n;
-                                node_taps<T, BASIS, UTERM>(cc, A.row[rr], colrel, rr - W.WP0, uv, m,
-                                                           n, wx, wy);
-                                ring_add<T, N, -1>(win, W, rg, m, n, wx, wy, lost, kChunk - 1 - k);
-                            }
-                        }
-                    }
-                    ring_final<T, N, -1>(win, W, rg, lost, kChunk - 1);
-#pragma unroll
-                    for (int k = 0; k < kHalo; ++k) yr[k] = yr[k + kChunk];
-#pragma unroll
-                    for (int k = kHalo; k < kChunk + kHalo; ++k) {
-                        const int rr = c0 + kChunk + k;
-                        if (rr < np) {
-                            const T ibv = rr < kPivots ? (T)A.piv[2 * rr + 1] : ib_inf;
-                            gv = (src[(size_t)rr * nx] - sixth * gv) * ibv;
-                        }
-                        yr[k] = gv;
-                    }
+                const int last_ph = (jb - ja) % N;
+                if (last_ph == 0) ring_final<T, N, -1, 0>(win, W, rg, lost);
+                if (last_ph == 1) ring_final<T, N, -1, 1>(win, W, rg, lost);
+                if constexpr (N > 2) {
+                    if (last_ph == 2) ring_final<T, N, -1, 2 % N>(win, W, rg, lost);
+                    if (last_ph == 3) ring_final<T, N, -1, 3 % N>(win, W, rg, lost);
                 }
             }
         }
@@ -609,7 +711,7 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const F
         // fold the guard columns onto the period: [-G, 0) -> [nx - G, nx), [nx, nx + G) -> [0, G)
         __syncthreads();
         for (int k = tid; k < TPe * G; k += blockDim.x) {
-            const int rr = k / G + G, c = k - (k / G) * G;
+            const int rr = k / G + Gp, c = k - (k / G) * G;
             T *row = win + (size_t)rr * W.ws;
             row[nx + c] += row[c];
             row[G + c] += row[G + nx + c];
@@ -628,7 +730,7 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const F
         const int L = full ? nx : TXe + 2 * D;
         int per = (L + 31) / 32, base = lane * per;   // same for every row (warps without rows too)
         for (int rr = warp; rr < TPe; rr += nwarps) {
-            const T *row = win + (size_t)(rr + G) * W.ws + G;
+            const T *row = win + (size_t)(rr + Gp) * W.ws + G;
             T *dst_row = A.dst + (size_t)(P0 + rr) * nx + X0 - D;
             T v[kXMax];
             solve_row_x<T>(row, L, full, lane, v, per, base);
@@ -661,14 +763,14 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const F
     } else {
         for (int k = tid; k < TXe * TPe; k += blockDim.x) {
             const int rr = k / TXe, c = k - rr * TXe;
-            const T v = win[(size_t)(rr + G) * W.ws + G + c];
+            const T v = win[(size_t)(rr + Gp) * W.ws + G + c];
             A.dst[(size_t)(P0 + rr) * nx + X0 + c] = v;
             bad |= !isfinite(v);
         }
         if (want_part)
             for (int c = tid; c < TXe; c += blockDim.x) {
                 T s = T(0), comp = T(0);
-                for (int rr = 0; rr < TPe; ++rr) kahan(s, comp, win[(size_t)(rr + G) * W.ws + G + c]);
+                for (int rr = 0; rr < TPe; ++rr) kahan(s, comp, win[(size_t)(rr + Gp) * W.ws + G + c]);
                 const double sum = (double)s - (double)comp;
                 const double2 t = A.csx[X0 + c];
                 pw += sum;
@@ -701,16 +803,16 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const F
 }
 
 template <typename T>
-size_t fused_smem_bytes(int ws, int wh)
+size_t fused_smem_bytes(int ws, int wh, int threads)
 {
-    return (size_t)ws * wh * sizeof(T);
+    return (size_t)ws * wh * sizeof(T) + (size_t)GRows<T>::value * threads * sizeof(T);
 }
 
 template <typename T>
 cudaError_t launch_step_fused(const FusedArgs<T> &a, int threads, cudaStream_t s)
 {
-    const int wh = a.tp + 2 * a.G;
-    const size_t smem = fused_smem_bytes<T>(a.ws, wh);
+    const int wh = a.tp + 2 * a.Gp;
+    const size_t smem = fused_smem_bytes<T>(a.ws, wh, threads);
     const int grid = a.ntx * a.ntp;
     const bool gal = a.g.basis == VP_BASIS_CUBIC_BSPLINE && a.g.projection == VP_PROJ_GALERKIN;
     const bool uterm = a.g.kind == VP_PUSH_FEL_DKD;
@@ -760,8 +862,8 @@ cudaError_t launch_lambda_p_mul(const T *w, T *s, int nx, int np, cudaStream_t s
     return cudaGetLastError();
 }
 
-template size_t fused_smem_bytes<float>(int, int);
-template size_t fused_smem_bytes<double>(int, int);
+template size_t fused_smem_bytes<float>(int, int, int);
+template size_t fused_smem_bytes<double>(int, int, int);
 template cudaError_t launch_step_fused<float>(const FusedArgs<float> &, int, cudaStream_t);
 template cudaError_t launch_step_fused<double>(const FusedArgs<double> &, int, cudaStream_t);
 template cudaError_t launch_lambda_p_mul<float>(const float *, float *, int, int, cudaStream_t);

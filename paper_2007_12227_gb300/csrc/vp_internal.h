@@ -105,7 +105,7 @@ struct FusedArgs {
     unsigned *err;
     Geometry g;
     int tx, tp, ntx, ntp;
-    int G;                  // guard band (cells) around the widened tile
+    int G, Gp;              // guard bands (cells) around the widened tile: columns, rows
     int ws;                 // window row stride (elements)
     int full_row;           // tiles span the whole x period (ntx == 1)
     int fel_partials;
@@ -125,7 +125,7 @@ size_t tiled_smem_bytes(int tx, int tp);
 template <typename T>
 cudaError_t launch_step_fused(const FusedArgs<T> &a, int threads, cudaStream_t s);
 template <typename T>
-size_t fused_smem_bytes(int ws, int wh);
+size_t fused_smem_bytes(int ws, int wh, int threads);
 constexpr int fused_halo(int precision) { return precision == VP_FP64 ? 28 : 14; }
 constexpr int kFusedMaxRow = 512; // longest window row one warp solves
 template <typename T>
