@@ -150,7 +150,7 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
             ftx = grid->nx;
         }
         if (!full && ftx + 2 * halo > kFusedMaxRow) ftx = kFusedMaxRow - 2 * halo;
-        ftp = std::min(ftp, grid->np);
+        ftp = std::min(std::min(ftp, grid->np), kFusedMaxTileP);
         const int WW = full ? grid->nx + 2 * G : ftx + 2 * halo + 2 * G;
         const int ws = (WW + 31) / 32 * 32 + 1;
         const int wsrc = (full ? grid->nx : ftx + 2 * halo) + 2 * R + 8;

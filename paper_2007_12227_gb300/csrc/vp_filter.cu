@@ -19,6 +19,7 @@
 #include <math.h>
 
 #include "vp_internal.h"
+#include "vp_sum.cuh"
 
 namespace vp {
 namespace {
@@ -113,15 +114,6 @@ constexpr int kPCols = 32;    // columns per warp
 constexpr int kPWarps = 4;    // warps per block (adjacent column groups)
 constexpr int kPChunk = 128;  // rows per chunk
 
-template <typename T>
-__device__ __forceinline__ void kahan_add(T &sum, T &comp, T v)
-{
-    const T y = v - comp;
-    const T t = sum + y;
-    comp = (t - sum) - y;
-    sum = t;
-}
-
 // piv[2 r] = c'_r (super-diagonal factor), piv[2 r + 1] = 1 / beta_r, r < kPivots;
 // piv[2 kPivots], piv[2 kPivots + 1] = their limits.
 template <typename T>
@@ -156,7 +148,7 @@ __global__ void __launch_bounds__(kPCols *kPWarps)
         }
     }
     // back substitution from fe - 1 (exact at the last row: w_{np-1} = g_{np-1})
-    T wsum = T(0), wcomp = T(0);
+    DSum<T> wacc;
     bool bad = false;
     if (valid) {
         T w = T(0);
@@ -167,7 +159,7 @@ __global__ void __launch_bounds__(kPCols *kPWarps)
             if (r < e) {
                 out[(size_t)r * nx + col] = w;
                 bad |= !isfinite(w);
-                if (want_part) kahan_add(wsum, wcomp, w);
+                if (want_part) wacc.add(w);
             }
         }
     }
@@ -175,7 +167,7 @@ __global__ void __launch_bounds__(kPCols *kPWarps)
     if (!want_part) return;
     double pw = 0.0, pc = 0.0, ps = 0.0;
     if (valid) {
-        pw = (double)wsum - (double)wcomp;
+        pw = wacc.value();
         const double2 t = csx[col];
         pc = pw * t.x;
         ps = pw * t.y;

@@ -31,6 +31,7 @@
 #include <math.h>
 
 #include "vp_internal.h"
+#include "vp_sum.cuh"
 
 namespace vp {
 namespace {
@@ -46,12 +47,7 @@ template <typename T>
 struct GRows {
     static constexpr int value = kC > Halo<T>::value ? kC : Halo<T>::value;
 };
-constexpr int kXMax = kFusedMaxRow / 32;
-
-template <int U>
-struct IC {
-    static constexpr int value = U;
-};
+constexpr int kXBig = kFusedMaxRow / 32;   // elements per lane for rows up to kFusedMaxRow
 
 template <typename T, int BASIS>
 struct FTaps;
@@ -129,15 +125,6 @@ __device__ void sin_range_f(double lo, double hi, float &smin, float &smax)
     if ((a <= h3 && h3 <= b) || (a <= h3 + twopi && h3 + twopi <= b)) smin = -1.f;
 }
 
-template <typename T>
-__device__ __forceinline__ void kahan(T &sum, T &comp, T v)
-{
-    const T y = v - comp;
-    const T t = sum + y;
-    comp = (t - sum) - y;
-    sum = t;
-}
-
 template <typename T, int N>
 struct Ring {
     T acc[N][N];  // [slot][column]
@@ -194,58 +181,54 @@ __device__ __forceinline__ void flush_row(T *win, const WinGeom &W, const T *acc
     }
 }
 
-// slot of tap row b at phase ph: (b + ph) % N ascending, (b - ph) % N descending
-template <int N, int DIR, int PH>
-__device__ __forceinline__ constexpr int slot(int b)
-{
-    return DIR > 0 ? (b + PH) % N : (b - PH % N + N) % N;
-}
-
-// Add one node (weights wx, wy; base window column m, row n) at static phase PH.
-// DIR = +1: base rows ascend between consecutive nodes; DIR = -1: they descend.
-template <typename T, int N, int DIR, int PH>
+// Add one node (weights wx, wy; base window column m, row n). acc[b] always holds
+// window row nb + b. DIR = +1: base rows ascend between consecutive nodes (the
+// bottom row leaves); DIR = -1: they descend (the top row leaves). The row shift
+// is folded into the accumulation: acc[b] = acc[b +/- 1] + wy[b] wx.
+template <typename T, int N, int DIR>
 __device__ __forceinline__ void ring_add(T *win, const WinGeom &W, Ring<T, N> &rg, int m, int n,
                                          const T *wx, const T *wy, double &lost)
 {
-    constexpr int PP = (PH + N - 1) % N;   // phase of the previous node
     const bool step_ok = rg.live && n == rg.nb + DIR;
     if (step_ok && (m == rg.mref + 1 || m == rg.mref - 1)) {
         // the base column moved by one: flush the column that leaves, shift the rest
-        const bool left = m > rg.mref;
+        if (m > rg.mref) {
 #pragma unroll
-        for (int b = 0; b < N; ++b) {
-            const int q = slot<N, DIR, PP>(b);
-            if (left) {
-                flush_cell<T>(win, W, rg.acc[q][0], rg.mref, rg.nb + b, lost);
+            for (int b = 0; b < N; ++b) {
+                flush_cell<T>(win, W, rg.acc[b][0], rg.mref, rg.nb + b, lost);
 #pragma unroll
-                for (int a = 0; a < N - 1; ++a) rg.acc[q][a] = rg.acc[q][a + 1];
-                rg.acc[q][N - 1] = T(0);
-            } else {
-                flush_cell<T>(win, W, rg.acc[q][N - 1], rg.mref + N - 1, rg.nb + b, lost);
+                for (int a = 0; a < N - 1; ++a) rg.acc[b][a] = rg.acc[b][a + 1];
+                rg.acc[b][N - 1] = T(0);
+            }
+        } else {
 #pragma unroll
-                for (int a = N - 1; a > 0; --a) rg.acc[q][a] = rg.acc[q][a - 1];
-                rg.acc[q][0] = T(0);
+            for (int b = 0; b < N; ++b) {
+                flush_cell<T>(win, W, rg.acc[b][N - 1], rg.mref + N - 1, rg.nb + b, lost);
+#pragma unroll
+                for (int a = N - 1; a > 0; --a) rg.acc[b][a] = rg.acc[b][a - 1];
+                rg.acc[b][0] = T(0);
             }
         }
         rg.mref = m;
         rg.col_ok = (unsigned)m <= (unsigned)(W.WW - N);   // overflow-safe for any m
     }
     if (step_ok && m == rg.mref) {
-        // the ring moves one row: flush the row leaving it, the entering row starts fresh
-        const int bl = DIR > 0 ? 0 : N - 1;           // leaving row, previous node's tap index
-        const int ql = slot<N, DIR, PP>(bl);
-        flush_row<T, N>(win, W, rg.acc[ql], rg.mref, rg.col_ok, rg.nb + bl, lost);
-        const int be = DIR > 0 ? N - 1 : 0;           // entering row, this node's tap index
+        if (DIR > 0) {
+            flush_row<T, N>(win, W, rg.acc[0], rg.mref, rg.col_ok, rg.nb, lost);
 #pragma unroll
-        for (int b = 0; b < N; ++b) {
-            const int q = slot<N, DIR, PH>(b);
-            if (b == be) {
+            for (int b = 0; b < N - 1; ++b)
 #pragma unroll
-                for (int a = 0; a < N; ++a) rg.acc[q][a] = wy[b] * wx[a];
-            } else {
+                for (int a = 0; a < N; ++a) rg.acc[b][a] = rg.acc[b + 1][a] + wy[b] * wx[a];
 #pragma unroll
-                for (int a = 0; a < N; ++a) rg.acc[q][a] += wy[b] * wx[a];
-            }
+            for (int a = 0; a < N; ++a) rg.acc[N - 1][a] = wy[N - 1] * wx[a];
+        } else {
+            flush_row<T, N>(win, W, rg.acc[N - 1], rg.mref, rg.col_ok, rg.nb + N - 1, lost);
+#pragma unroll
+            for (int b = N - 1; b > 0; --b)
+#pragma unroll
+                for (int a = 0; a < N; ++a) rg.acc[b][a] = rg.acc[b - 1][a] + wy[b] * wx[a];
+#pragma unroll
+            for (int a = 0; a < N; ++a) rg.acc[0][a] = wy[0] * wx[a];
         }
         rg.nb = n;
         return;
@@ -253,32 +236,24 @@ __device__ __forceinline__ void ring_add(T *win, const WinGeom &W, Ring<T, N> &r
     // anything else (first node, a jump): flush the whole ring and restart
     if (rg.live) {
 #pragma unroll
-        for (int b = 0; b < N; ++b) {
-            const int q = slot<N, DIR, PP>(b);
-            flush_row<T, N>(win, W, rg.acc[q], rg.mref, rg.col_ok, rg.nb + b, lost);
-        }
+        for (int b = 0; b < N; ++b) flush_row<T, N>(win, W, rg.acc[b], rg.mref, rg.col_ok, rg.nb + b, lost);
     }
 #pragma unroll
-    for (int b = 0; b < N; ++b) {
-        const int q = slot<N, DIR, PH>(b);
+    for (int b = 0; b < N; ++b)
 #pragma unroll
-        for (int a = 0; a < N; ++a) rg.acc[q][a] = wy[b] * wx[a];
-    }
+        for (int a = 0; a < N; ++a) rg.acc[b][a] = wy[b] * wx[a];
     rg.mref = m;
     rg.nb = n;
-    rg.col_ok = (unsigned)m <= (unsigned)(W.WW - N);   // overflow-safe for any m
+    rg.col_ok = (unsigned)m <= (unsigned)(W.WW - N);
     rg.live = true;
 }
 
-template <typename T, int N, int DIR, int PH>
+template <typename T, int N>
 __device__ __forceinline__ void ring_final(T *win, const WinGeom &W, Ring<T, N> &rg, double &lost)
 {
     if (!rg.live) return;
 #pragma unroll
-    for (int b = 0; b < N; ++b) {
-        const int q = slot<N, DIR, PH>(b);
-        flush_row<T, N>(win, W, rg.acc[q], rg.mref, rg.col_ok, rg.nb + b, lost);
-    }
+    for (int b = 0; b < N; ++b) flush_row<T, N>(win, W, rg.acc[b], rg.mref, rg.col_ok, rg.nb + b, lost);
     rg.live = false;
 }
 
@@ -343,7 +318,7 @@ __device__ __forceinline__ void node_taps(const ColC<T> &c, const RowEntry<T> &r
 // shared memory, by one warp. Returns each lane's elements base .. base + per - 1 in v.
 // cyclic: the row is one whole period; else the row is padded by the halo on both
 // sides and the recurrences start from zero at its ends (truncation |z|^halo).
-template <typename T>
+template <typename T, int kXMax>
 __device__ void solve_row_x(const T *row, int L, bool cyclic, int lane, T *v, int &per, int &base)
 {
     per = (L + 31) / 32;
@@ -441,6 +416,31 @@ __device__ void solve_row_x(const T *row, int L, bool cyclic, int lane, T *v, in
 
 }  // namespace
 
+// Lambda_x solve of the tile's window rows (one warp per row) and the tile store.
+template <typename T, int KX>
+__device__ __forceinline__ void gal_rows(T *win, const WinGeom &W, T *dst, int L, bool full, int D,
+                                         int G, int Gp, int TXe, int TPe, int P0, int X0, int nx,
+                                         bool want_part, int warp, int nwarps, int lane, bool &bad)
+{
+    for (int rr = warp; rr < TPe; rr += nwarps) {
+        T *row = win + (size_t)(rr + Gp) * W.ws + G;
+        T *dst_row = dst + (size_t)(P0 + rr) * nx + X0 - D;
+        T v[KX];
+        int per, base;
+        solve_row_x<T, KX>(row, L, full, lane, v, per, base);
+        __syncwarp();
+#pragma unroll
+        for (int k = 0; k < KX; ++k) {
+            const int c = base + k;
+            if (k < per && c >= D && c < D + TXe) {
+                dst_row[c] = v[k];
+                bad |= !isfinite(v[k]);
+                if (want_part) row[c] = v[k];   // keep s for the column sums
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 template <typename T, int BASIS, bool GAL, bool UTERM>
 __global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const FusedArgs<T> A)
@@ -455,6 +455,7 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const F
     __shared__ double s_r4[4][kFusedMaxThreads / 32];
     // Thomas pivots of tridiag(1/6, 2/3, 1/6) in T: entry kPivots holds the limit
     __shared__ T piv_cp[kPivots + 1], piv_ib[kPivots + 1];
+    __shared__ T sig_s[kFusedMaxTileP];   // column-sum weights of Lambda_p^{-1} for the tile rows
 
     const Geometry &g = A.g;
     const int nx = g.nx, np = g.np;
@@ -485,6 +486,8 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const F
         piv_cp[k] = (T)A.piv[2 * k];
         piv_ib[k] = (T)A.piv[2 * k + 1];
     }
+    if (GAL && A.fel_partials)
+        for (int k = tid; k < TPe; k += blockDim.x) sig_s[k] = (T)A.sigma[P0 + k];
     if (tid == 0) {
         s_ia = 0x7fffffff;
         s_ib = -0x7fffffff;
@@ -608,31 +611,14 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const F
                 for (int a = 0; a < N; ++a) rg.acc[q][a] = T(0);
             T wx[N], wy[N];
             if (!GAL) {
-                // ascending walk in groups of N rows; each phase is a template constant
-                auto row_step = [&](auto ph, int jj) {
-                    constexpr int u = decltype(ph)::value;
-                    if (jj <= jb) {
-                        const T w = src[(size_t)jj * nx];
-                        int m, n;
-                        node_taps<T, BASIS, UTERM>(cc, A.row[jj], colrel, jj - W.WP0, w, m, n, wx, wy);
-                        ring_add<T, N, 1, u>(win, W, rg, m, n, wx, wy, lost);
-                    }
-                };
-                for (int j = ja; j <= jb; j += N) {
-                    row_step(IC<0>{}, j);
-                    row_step(IC<1>{}, j + 1);
-                    if constexpr (N > 2) {
-                        row_step(IC<2>{}, j + 2);
-                        row_step(IC<3>{}, j + 3);
-                    }
+                const T *sp = src + (size_t)ja * nx;
+#pragma unroll 2
+                for (int jj = ja; jj <= jb; ++jj, sp += nx) {
+                    int m, n;
+                    node_taps<T, BASIS, UTERM>(cc, A.row[jj], colrel, jj - W.WP0, *sp, m, n, wx, wy);
+                    ring_add<T, N, 1>(win, W, rg, m, n, wx, wy, lost);
                 }
-                const int last_ph = (jb - ja) % N;
-                if (last_ph == 0) ring_final<T, N, 1, 0>(win, W, rg, lost);
-                if (last_ph == 1) ring_final<T, N, 1, 1>(win, W, rg, lost);
-                if constexpr (N > 2) {
-                    if (last_ph == 2) ring_final<T, N, 1, 2 % N>(win, W, rg, lost);
-                    if (last_ph == 3) ring_final<T, N, 1, 3 % N>(win, W, rg, lost);
-                }
+                ring_final<T, N>(win, W, rg, lost);
             } else {
                 // Lambda_p^{-1} s by the Thomas algorithm, walked downwards in chunks of
                 // kC rows: forward sweep g_j = (s_j - g_{j-1}/6) / beta_j from kHalo rows
@@ -646,55 +632,37 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const F
                     const int top = min(np - 1, jb + kHalo);
                     if (top > jb) {
                         int rr = max(0, jb + 1 - kHalo);
+                        const T *sp = src + (size_t)rr * nx;
                         T gv = T(0);
-#pragma unroll 4
-                        for (; rr <= jb; ++rr)
-                            gv = (src[(size_t)rr * nx] - sixth * gv) * piv_ib[min(rr, kPivots)];
-#pragma unroll 4
-                        for (; rr <= top; ++rr) {
-                            gv = (src[(size_t)rr * nx] - sixth * gv) * piv_ib[min(rr, kPivots)];
+                        for (; rr <= jb; ++rr, sp += nx) gv = (*sp - sixth * gv) * piv_ib[min(rr, kPivots)];
+                        for (; rr <= top; ++rr, sp += nx) {
+                            gv = (*sp - sixth * gv) * piv_ib[min(rr, kPivots)];
                             gc[(rr - jb - 1) * nth] = gv;
                         }
                         for (rr = top; rr > jb; --rr) uv = gc[(rr - jb - 1) * nth] - piv_cp[min(rr, kPivots)] * uv;
                     }
                 }
-                auto row_step = [&](auto ph, int r, int c_lo) {
-                    constexpr int u = decltype(ph)::value;
-                    if (r >= c_lo) {
-                        uv = gc[(r - c_lo) * nth] - piv_cp[min(r, kPivots)] * uv;
-                        int m, n;
-                        node_taps<T, BASIS, UTERM>(cc, A.row[r], colrel, r - W.WP0, uv, m, n, wx, wy);
-                        ring_add<T, N, -1, u>(win, W, rg, m, n, wx, wy, lost);
-                    }
-                };
                 for (int c_hi = jb; c_hi >= ja; c_hi -= kC) {
                     const int c_lo = max(ja, c_hi - kC + 1);
                     int rr = max(0, c_lo - kHalo);
+                    const T *sp = src + (size_t)rr * nx;
                     T gv = T(0);
 #pragma unroll 4
-                    for (; rr < c_lo; ++rr)
-                        gv = (src[(size_t)rr * nx] - sixth * gv) * piv_ib[min(rr, kPivots)];
+                    for (; rr < c_lo; ++rr, sp += nx) gv = (*sp - sixth * gv) * piv_ib[min(rr, kPivots)];
 #pragma unroll 4
-                    for (; rr <= c_hi; ++rr) {
-                        gv = (src[(size_t)rr * nx] - sixth * gv) * piv_ib[min(rr, kPivots)];
+                    for (; rr <= c_hi; ++rr, sp += nx) {
+                        gv = (*sp - sixth * gv) * piv_ib[min(rr, kPivots)];
                         gc[(rr - c_lo) * nth] = gv;
                     }
-                    for (int r4 = c_hi; r4 >= c_lo; r4 -= N) {
-                        row_step(IC<0>{}, r4, c_lo);
-                        row_step(IC<1>{}, r4 - 1, c_lo);
-                        if constexpr (N > 2) {
-                            row_step(IC<2>{}, r4 - 2, c_lo);
-                            row_step(IC<3>{}, r4 - 3, c_lo);
-                        }
+#pragma unroll 2
+                    for (int r = c_hi; r >= c_lo; --r) {
+                        uv = gc[(r - c_lo) * nth] - piv_cp[min(r, kPivots)] * uv;
+                        int m, n;
+                        node_taps<T, BASIS, UTERM>(cc, A.row[r], colrel, r - W.WP0, uv, m, n, wx, wy);
+                        ring_add<T, N, -1>(win, W, rg, m, n, wx, wy, lost);
                     }
                 }
-                const int last_ph = (jb - ja) % N;
-                if (last_ph == 0) ring_final<T, N, -1, 0>(win, W, rg, lost);
-                if (last_ph == 1) ring_final<T, N, -1, 1>(win, W, rg, lost);
-                if constexpr (N > 2) {
-                    if (last_ph == 2) ring_final<T, N, -1, 2 % N>(win, W, rg, lost);
-                    if (last_ph == 3) ring_final<T, N, -1, 3 % N>(win, W, rg, lost);
-                }
+                ring_final<T, N>(win, W, rg, lost);
             }
         }
     }
@@ -724,42 +692,13 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const F
     bool bad = false;
     double pw = 0.0, pc = 0.0, ps = 0.0;
     if (GAL) {
-        T cs[kXMax];
-#pragma unroll
-        for (int k = 0; k < kXMax; ++k) cs[k] = T(0);
         const int L = full ? nx : TXe + 2 * D;
-        int per = (L + 31) / 32, base = lane * per;   // same for every row (warps without rows too)
-        for (int rr = warp; rr < TPe; rr += nwarps) {
-            const T *row = win + (size_t)(rr + Gp) * W.ws + G;
-            T *dst_row = A.dst + (size_t)(P0 + rr) * nx + X0 - D;
-            T v[kXMax];
-            solve_row_x<T>(row, L, full, lane, v, per, base);
-            const T sig = want_part ? (T)A.sigma[P0 + rr] : T(0);
-#pragma unroll
-            for (int k = 0; k < kXMax; ++k) {
-                const int c = base + k;
-                if (k < per && c >= D && c < D + TXe) {
-                    dst_row[c] = v[k];
-                    bad |= !isfinite(v[k]);
-                    cs[k] += sig * v[k];
-                }
-            }
-        }
-        if (want_part) {
-            __syncthreads();   // the window is free now: per-warp column sums go there
-            T *slice = win + (size_t)warp * (L + 32);
-            for (int k = 0; k < kXMax; ++k)
-                if (k < per && base + k < L) slice[base + k] = cs[k];
-            __syncthreads();
-            for (int c = D + tid; c < D + TXe; c += blockDim.x) {
-                double sum = 0.0;
-                for (int w = 0; w < nwarps; ++w) sum += (double)win[(size_t)w * (L + 32) + c];
-                const double2 t = A.csx[X0 + c - D];
-                pw += sum;
-                pc += sum * t.x;
-                ps += sum * t.y;
-            }
-        }
+        if (L <= 256)
+            gal_rows<T, 8>(win, W, A.dst, L, full, D, G, Gp, TXe, TPe, P0, X0, nx, want_part, warp,
+                           nwarps, lane, bad);
+        else
+            gal_rows<T, kXBig>(win, W, A.dst, L, full, D, G, Gp, TXe, TPe, P0, X0, nx, want_part,
+                               warp, nwarps, lane, bad);
     } else {
         for (int k = tid; k < TXe * TPe; k += blockDim.x) {
             const int rr = k / TXe, c = k - rr * TXe;
@@ -767,16 +706,23 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const F
             A.dst[(size_t)(P0 + rr) * nx + X0 + c] = v;
             bad |= !isfinite(v);
         }
-        if (want_part)
-            for (int c = tid; c < TXe; c += blockDim.x) {
-                T s = T(0), comp = T(0);
-                for (int rr = 0; rr < TPe; ++rr) kahan(s, comp, win[(size_t)(rr + Gp) * W.ws + G + c]);
-                const double sum = (double)s - (double)comp;
-                const double2 t = A.csx[X0 + c];
-                pw += sum;
-                pc += sum * t.x;
-                ps += sum * t.y;
+    }
+    if (want_part) {
+        // FEL: column sums of w over the tile (Galerkin: sum_j w_ij = sum_j sigma_j s_ij)
+        __syncthreads();
+        for (int c = tid; c < TXe; c += blockDim.x) {
+            DSum<T> acc;
+            for (int rr = 0; rr < TPe; ++rr) {
+                const T v = win[(size_t)(rr + Gp) * W.ws + G + D + c];
+                if (GAL) acc.add_prod(sig_s[rr], v);
+                else acc.add(v);
             }
+            const double sum = acc.value();
+            const double2 t = A.csx[X0 + c];
+            pw += sum;
+            pc += sum * t.x;
+            ps += sum * t.y;
+        }
     }
     if (bad) atomicOr(A.err, ERRF_NONFINITE);
 

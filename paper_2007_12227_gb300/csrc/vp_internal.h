@@ -128,6 +128,7 @@ template <typename T>
 size_t fused_smem_bytes(int ws, int wh, int threads);
 constexpr int fused_halo(int precision) { return precision == VP_FP64 ? 28 : 14; }
 constexpr int kFusedMaxRow = 512; // longest window row one warp solves
+constexpr int kFusedMaxTileP = 256; // tallest tile of the fused kernel
 template <typename T>
 cudaError_t launch_lambda_p_mul(const T *w, T *s, int nx, int np, cudaStream_t st);
 

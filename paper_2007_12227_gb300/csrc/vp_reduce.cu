@@ -13,20 +13,12 @@
 #include <math.h>
 
 #include "vp_internal.h"
+#include "vp_sum.cuh"
 
 namespace vp {
 namespace {
 
 constexpr int kRedThreads = 256;
-
-template <typename T>
-__device__ __forceinline__ void kahan_add(T &sum, T &comp, T v)
-{
-    const T y = v - comp;
-    const T t = sum + y;
-    comp = (t - sum) - y;
-    sum = t;
-}
 
 // one block per 32-column strip x row chunk: column sums (compensated) then x cos/sin
 constexpr int kFelRows = 256;
@@ -40,10 +32,10 @@ __global__ void fel_partials_kernel(const T *__restrict__ w, int nx, int np,
     const int col = blockIdx.x * 32 + lane;
     const int r0 = blockIdx.y * kFelRows;
     const int r1 = min(r0 + kFelRows, np);
-    T s = T(0), c = T(0);
+    DSum<T> acc;
     if (col < nx)
-        for (int r = r0 + wy; r < r1; r += kRedThreads / 32) kahan_add(s, c, w[(size_t)r * nx + col]);
-    double pw = (double)s - (double)c, pc = 0.0, ps = 0.0;
+        for (int r = r0 + wy; r < r1; r += kRedThreads / 32) acc.add(w[(size_t)r * nx + col]);
+    double pw = acc.value(), pc = 0.0, ps = 0.0;
     if (col < nx) {
         const double2 t = csx[col];
         pc = pw * t.x;

@@ -22,6 +22,7 @@
 #include <math.h>
 
 #include "vp_internal.h"
+#include "vp_sum.cuh"
 
 namespace vp {
 namespace {
@@ -98,15 +99,6 @@ __device__ void sin_range(double lo, double hi, double &smin, double &smax)
     if (hpi + kmax * twopi <= hi) smax = 1.0;
     const double kmin = ceil((lo + hpi) / twopi);
     if (-hpi + kmin * twopi <= hi) smin = -1.0;
-}
-
-template <typename T>
-__device__ __forceinline__ void kahan_add(T &sum, T &comp, T v)
-{
-    const T y = v - comp;
-    const T t = sum + y;
-    comp = (t - sum) - y;
-    sum = t;
 }
 
 template <typename T, int BASIS>
@@ -276,12 +268,9 @@ __global__ void __launch_bounds__(kThreads) step_tiled_kernel(const StepArgs<T> 
     if (A.fel_partials) {
         // column-major walk so that each thread keeps one column's cos/sin
         for (int cidx = threadIdx.x; cidx < TXe; cidx += blockDim.x) {
-            T cs = T(0), cc = T(0);
-            for (int rr = 0; rr < TPe; ++rr) {
-                const T v = win[(size_t)rr * TX + cidx];
-                kahan_add(cs, cc, v);
-            }
-            const double colsum = (double)cs - (double)cc;
+            DSum<T> acc;
+            for (int rr = 0; rr < TPe; ++rr) acc.add(win[(size_t)rr * TX + cidx]);
+            const double colsum = acc.value();
             const double2 t = A.csx[X0 + cidx];
             pw += colsum;
             pc += colsum * t.x;
