@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-extra", action="store_true")
     ap.add_argument("--size", type=int, default=8192, help="mesh side (default 8192)")
+    ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-serve", action="store_true")
+    ap.add_argument("--batch-steps", type=int, default=40)
     return ap.parse_args()
 
 
@@ -140,6 +143,81 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def bench_batch(V, torch, stream, batch_steps=40, seq_rounds=5):
+    """256 ragged instances (pendulum / FEL, 64^2 .. 2048^2): one persistent launch per
+    step replayed from a CUDA graph, against the same instances stepped one by one."""
+    wls = I.batch_256()
+    sims = []
+    for wl in wls:
+        sm = V.Sim(wl.grid, wl.basis, wl.pusher, precision=V.VP_FP32, stream=stream)
+        sm.set_f(I.make_f0(wl).astype(np.float32))
+        sims.append(sm)
+    nodes = sum(w.grid.nodes for w in wls)
+    batch = V.Batch(sims, stream=stream)
+    batch.step(3)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    batch.step(batch_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    bms = e0.elapsed_time(e1) / batch_steps
+    # sequential plain solves: every instance advanced by its own vp_step calls
+    for sm in sims:
+        sm.step(1)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(seq_rounds):
+        for sm in sims:
+            sm.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sms = e0.elapsed_time(e1) / seq_rounds
+    batch.close()
+    for sm in sims:
+        sm.close()
+    return {"instances": len(wls), "nodes_per_step": nodes,
+            "batched_node_updates_per_s": nodes / (bms * 1e-3), "batched_ms_per_step": bms,
+            "sequential_node_updates_per_s": nodes / (sms * 1e-3), "sequential_ms_per_step": sms,
+            "speedup": sms / bms, "graph": True, "steps_timed": batch_steps}
+
+
+def bench_serve(V, torch, stream, count=60, budget_gb=150.0):
+    """Served form: the first `count` requests of the Poisson trace (500 requests/s, meshes
+    128^2 .. 4096^2 log-uniform, 100 .. 5000 steps, pendulum / FEL), arriving in real time;
+    continuous batching under an HBM budget. Latency = finish - arrival."""
+    reqs = I.serving_trace(count=count)
+    f0s = [I.make_f0(r.workload).astype(np.float32) for r in reqs]
+    free = torch.cuda.mem_get_info()[0]
+    arena = int(min(budget_gb * 1e9, 0.8 * free))
+    srv = V.Server(arena, budget_bytes=arena, slice_steps=100, stream=stream)
+    t0 = srv.clock()
+    nxt = 0
+    done = {}
+    while len(done) < len(reqs):
+        now = srv.clock() - t0
+        while nxt < len(reqs) and reqs[nxt].arrival <= now:
+            r = reqs[nxt]
+            srv.submit(r.rid, r.workload.grid, r.workload.basis, r.workload.pusher, f0s[nxt],
+                       r.workload.steps)
+            nxt += 1
+        q, a = srv.run(1)
+        for res in srv.poll():
+            done[res["id"]] = res
+        if q == 0 and a == 0 and nxt < len(reqs):
+            time.sleep(max(0.0, reqs[nxt].arrival - (srv.clock() - t0)))
+    wall = srv.clock() - t0
+    srv.close()
+    lat = sorted(done[r.rid]["t_finish"] - (t0 + r.arrival) for r in reqs)
+    work = sum(r.workload.grid.nodes * r.workload.steps for r in reqs)
+    return {"requests": count, "trace": "Poisson 500/s, seed 2007122272 (prefix)",
+            "node_updates": work, "wall_s": wall, "node_updates_per_s": work / wall,
+            "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+            "budget_bytes": arena,
+            "batched_fraction": sum(1 for d in done.values() if d["batched"]) / len(done)}
 
 
 def cpu_baseline(wl):
@@ -313,6 +391,11 @@ def main():
                            "ms_per_step": fms, "steps_timed": nf,
                            "phase_ms": dict(zip(names, [p / 200 for p in fsim.step_profiled(200)]))}
         fsim.close()
+
+    if not args.skip_extra and rank == 0 and not args.skip_batch:
+        extra["batch_256"] = bench_batch(V, torch, stream, args.batch_steps)
+    if not args.skip_extra and rank == 0 and not args.skip_serve:
+        extra["served"] = bench_serve(V, torch, stream)
 
     cpu = None
     if rank == 0 and not args.skip_cpu:

@@ -180,6 +180,82 @@ void vp_destroy(vp_sim *sim);
 const char *vp_last_error(const vp_sim *sim);
 const char *vp_status_string(vp_status status);
 
+/* ---------------------------------------------------------------- batching
+ * Many independent simulations (different meshes and pushers, same precision,
+ * basis and projection, all on the one-pass kernel) advance together: one
+ * persistent launch per step takes (simulation, tile) items from a device work
+ * queue, then one launch finishes every simulation's step (FEL field update or
+ * step counter). Steady-state steps replay a captured CUDA graph. Each
+ * simulation's weights, field and moments stay readable through the vp_sim
+ * calls; a simulation must not be stepped on its own while a batch step of it
+ * is in flight. The batch keeps its tables in caller-owned device memory. */
+typedef struct vp_batch vp_batch;
+
+vp_status vp_batch_workspace_size(vp_sim *const *sims, int32_t count, size_t *bytes);
+/* sims: count simulations (kept by the caller, alive while the batch exists). */
+vp_status vp_batch_create(vp_sim *const *sims, int32_t count, void *stream, void *workspace,
+                          size_t workspace_bytes, vp_batch **out);
+/* Advance every simulation of the batch n steps (asynchronous). use_graph = 1
+ * replays one captured step graph per step (captured on the first call). */
+vp_status vp_batch_step(vp_batch *batch, int32_t n, int32_t use_graph);
+vp_status vp_batch_sync(vp_batch *batch);
+void vp_batch_destroy(vp_batch *batch);
+const char *vp_batch_last_error(const vp_batch *batch);
+
+/* ----------------------------------------------------------------- serving
+ * A request loop with continuous batching: requests (mesh, pusher, initial
+ * weights, step count) arrive at any time; each scheduling round admits queued
+ * requests first-in first-out while their device memory fits the budget (a
+ * first-fit allocator over a caller-owned arena), advances all admitted
+ * requests together as one batch for a slice of steps, and retires those that
+ * are done (moments and, on request, the final weights are kept for the
+ * caller; the memory returns to the arena). Requests that cannot join a batch
+ * (FP64, or meshes the one-pass kernel does not take) are stepped on their own
+ * in the same round. Single host thread; times are host steady-clock seconds. */
+typedef struct vp_server vp_server;
+
+typedef struct vp_server_opts {
+    size_t budget_bytes;   /* device memory the server may hold (<= arena bytes) */
+    int32_t slice_steps;   /* steps per round at most (0 = 50) */
+    int32_t max_active;    /* admitted requests at most (0 = 4096) */
+    void *stream;          /* cudaStream_t of all server work */
+} vp_server_opts;
+
+typedef struct vp_request {
+    uint64_t id;           /* caller's identifier, reported back */
+    vp_grid grid;
+    int32_t basis;
+    vp_pusher pusher;
+    int32_t precision, projection;
+    int32_t steps;         /* steps to advance */
+    int32_t keep_f;        /* 1: keep the final weights for vp_server_take_f */
+    const void *f0;        /* host initial weights [np][nx], copied by vp_server_submit */
+    int32_t f0_dtype;      /* VP_FP32 or VP_FP64 */
+} vp_request;
+
+typedef struct vp_result {
+    uint64_t id;
+    int32_t status;        /* vp_status of the request */
+    int32_t batched;       /* advanced inside a batch */
+    double t_submit, t_admit, t_finish;
+    vp_moments_t moments;  /* at completion */
+} vp_result;
+
+vp_status vp_server_create(const vp_server_opts *opts, void *arena, size_t arena_bytes,
+                           vp_server **out);
+vp_status vp_server_submit(vp_server *srv, const vp_request *req);
+/* Run up to rounds scheduling rounds (stops early when nothing is queued or active).
+ * *queued and *active (may be NULL) receive the counts after the last round. */
+vp_status vp_server_run(vp_server *srv, int32_t rounds, int32_t *queued, int32_t *active);
+/* Move up to max finished results into out; *count receives how many. */
+vp_status vp_server_poll(vp_server *srv, vp_result *out, int32_t max, int32_t *count);
+/* Final weights of a finished request submitted with keep_f (then released). */
+vp_status vp_server_take_f(vp_server *srv, uint64_t id, void *host, int32_t dtype, size_t n);
+/* Host steady-clock seconds, the clock of vp_result. */
+double vp_server_clock(void);
+void vp_server_destroy(vp_server *srv);
+const char *vp_server_last_error(const vp_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

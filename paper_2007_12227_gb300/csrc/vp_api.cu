@@ -859,3 +859,243 @@ void vp_destroy(vp_sim *s) { delete s; }
 const char *vp_last_error(const vp_sim *s) { return s ? s->msg : "NULL simulation"; }
 
 }  // extern "C"
+
+// ============================================================================ batching
+struct vp_batch {
+    std::vector<vp_sim *> sims;
+    cudaStream_t stream;
+    char *ws;
+    FusedArgs<float> *d_args;
+    int *d_parity;
+    int2 *d_items;
+    int *d_counter;
+    BatchFinal *d_fin;
+    int nitems, ninst, threads, grid, basis, projection;
+    size_t smem;
+    cudaGraphExec_t graph;
+    bool have_graph;
+    std::vector<int> host_parity;
+    char msg[512];
+};
+
+namespace {
+
+struct BatchLayout {
+    size_t args, parity, items, counter, fin, total;
+};
+
+vp_status batch_layout(vp_sim *const *sims, int count, BatchLayout *L, int *nitems, char *msg)
+{
+    if (!sims || count < 1) return fail(msg, VP_ERR_ARG, "batch needs at least one simulation");
+    int items = 0;
+    for (int k = 0; k < count; ++k) {
+        const vp_sim *s = sims[k];
+        if (!s) return fail(msg, VP_ERR_ARG, "simulation %d is NULL", k);
+        const Plan &P = s->P;
+        const Plan &P0 = sims[0]->P;
+        if (P.kernel != VP_KERNEL_FUSED)
+            return fail(msg, VP_ERR_UNSUPPORTED, "simulation %d does not use the one-pass kernel", k);
+        if (P.precision != VP_FP32)
+            return fail(msg, VP_ERR_UNSUPPORTED, "batches hold FP32 simulations (simulation %d)", k);
+        if (P.g.basis != P0.g.basis || P.g.projection != P0.g.projection)
+            return fail(msg, VP_ERR_ARG, "simulation %d differs in basis or projection", k);
+        items += P.ntx * P.ntp;
+    }
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    };
+    L->args = take(sizeof(FusedArgs<float>) * 2 * count);
+    L->parity = take(sizeof(int) * count);
+    L->items = take(sizeof(int2) * items);
+    L->counter = take(sizeof(int) * 4);
+    L->fin = take(sizeof(BatchFinal) * count);
+    L->total = off;
+    *nitems = items;
+    return VP_OK;
+}
+
+#define VP_BCUDA(b, ...)                                                                   \
+    do {                                                                                   \
+        cudaError_t e_ = (__VA_ARGS__);                                                    \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(b->msg, VP_ERR_CUDA, "%s: %s", #__VA_ARGS__, cudaGetErrorString(e_)); \
+    } while (0)
+
+vp_status batch_enqueue_step(vp_batch *b)
+{
+    VP_BCUDA(b, cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream));
+    VP_BCUDA(b, launch_step_fused_batch<float>(b->d_args, b->d_parity, b->d_items, b->nitems,
+                                               b->d_counter, b->basis, b->projection, b->smem,
+                                               b->threads, b->grid, b->stream));
+    VP_BCUDA(b, launch_batch_finalize(b->d_fin, b->ninst, b->d_parity, b->stream));
+    return VP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+vp_status vp_batch_workspace_size(vp_sim *const *sims, int32_t count, size_t *bytes)
+{
+    if (!bytes) return VP_ERR_ARG;
+    BatchLayout L;
+    int n;
+    vp_status st = batch_layout(sims, count, &L, &n, nullptr);
+    if (st == VP_OK) *bytes = L.total;
+    return st;
+}
+
+vp_status vp_batch_create(vp_sim *const *sims, int32_t count, void *stream, void *workspace,
+                          size_t workspace_bytes, vp_batch **out)
+{
+    if (!out) return VP_ERR_ARG;
+    *out = nullptr;
+    vp_batch *b = new (std::nothrow) vp_batch();
+    if (!b) return VP_ERR_ARG;
+    BatchLayout L;
+    int nitems = 0;
+    vp_status st = batch_layout(sims, count, &L, &nitems, b->msg);
+    if (st != VP_OK) {
+        delete b;
+        return st;
+    }
+    if (!workspace || (reinterpret_cast<uintptr_t>(workspace) % kAlign) || workspace_bytes < L.total) {
+        delete b;
+        return VP_ERR_WORKSPACE;
+    }
+    b->sims.assign(sims, sims + count);
+    b->stream = static_cast<cudaStream_t>(stream);
+    b->ws = static_cast<char *>(workspace);
+    b->d_args = reinterpret_cast<FusedArgs<float> *>(b->ws + L.args);
+    b->d_parity = reinterpret_cast<int *>(b->ws + L.parity);
+    b->d_items = reinterpret_cast<int2 *>(b->ws + L.items);
+    b->d_counter = reinterpret_cast<int *>(b->ws + L.counter);
+    b->d_fin = reinterpret_cast<BatchFinal *>(b->ws + L.fin);
+    b->nitems = nitems;
+    b->ninst = count;
+    b->basis = sims[0]->P.g.basis;
+    b->projection = sims[0]->P.g.projection;
+    b->have_graph = false;
+    // tables: arguments for both buffer parities, the work queue (largest tiles first), finals
+    std::vector<FusedArgs<float>> args(2 * count);
+    std::vector<BatchFinal> fin(count);
+    std::vector<int> order(count);
+    b->threads = 32;
+    b->smem = 0;
+    for (int k = 0; k < count; ++k) {
+        vp_sim *s = sims[k];
+        const Plan &P = s->P;
+        args[2 * k] = fused_args<float>(s, s->f(0), s->f(1));
+        args[2 * k + 1] = fused_args<float>(s, s->f(1), s->f(0));
+        b->threads = std::max(b->threads, P.threads);
+        order[k] = k;
+        fin[k].state = s->ptr<double>(P.L.state);
+        fin[k].part = s->ptr<double>(P.L.part);
+        fin[k].hist = s->ptr<double>(P.L.hist);
+        fin[k].nparts = P.ntx * P.ntp;
+        fin[k].hist_cap = P.hist_cap;
+        fin[k].fel = P.fel ? 1 : 0;
+        fin[k].dt = P.g.dt;
+    }
+    for (int k = 0; k < count; ++k) {
+        const Plan &P = sims[k]->P;
+        b->smem = std::max(b->smem, fused_smem_bytes<float>(P.ws, P.tp + 2 * P.Gp, b->threads));
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        const Plan &A = sims[a]->P, &C = sims[c]->P;
+        return (size_t)A.tx * A.tp > (size_t)C.tx * C.tp;
+    });
+    std::vector<int2> items;
+    items.reserve(nitems);
+    for (int k : order)
+        for (int t = 0; t < sims[k]->P.ntx * sims[k]->P.ntp; ++t) items.push_back(make_int2(k, t));
+    cudaError_t e = cudaSuccess;
+    int dev = 0, nsm = 0, per_sm = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_args, args.data(), sizeof(FusedArgs<float>) * args.size(),
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_items, items.data(), sizeof(int2) * items.size(),
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_fin, fin.data(), sizeof(BatchFinal) * fin.size(),
+                            cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        delete b;
+        return VP_ERR_CUDA;
+    }
+    // persistent grid: as many CTAs as fit on the device at once
+    per_sm = b->smem > 0 ? (int)std::min<size_t>(2, (size_t)(224 * 1024) / (b->smem + 2048)) : 2;
+    if (per_sm < 1) per_sm = 1;
+    b->grid = std::max(1, std::min(nitems, nsm * per_sm));
+    e = launch_step_fused_batch<float>(nullptr, nullptr, nullptr, 0, nullptr, b->basis, b->projection,
+                                       b->smem, b->threads, 0, b->stream);
+    if (e != cudaSuccess) {
+        delete b;
+        return VP_ERR_CUDA;
+    }
+    *out = b;
+    return VP_OK;
+}
+
+vp_status vp_batch_step(vp_batch *b, int32_t n, int32_t use_graph)
+{
+    if (!b) return VP_ERR_ARG;
+    if (n < 0) return fail(b->msg, VP_ERR_ARG, "negative step count");
+    b->host_parity.resize(b->ninst);
+    for (int k = 0; k < b->ninst; ++k) {
+        if (!b->sims[k]->f_set) return fail(b->msg, VP_ERR_STATE, "simulation %d has no weights", k);
+        b->host_parity[k] = b->sims[k]->cur;
+    }
+    VP_BCUDA(b, cudaMemcpyAsync(b->d_parity, b->host_parity.data(), sizeof(int) * b->ninst,
+                                cudaMemcpyHostToDevice, b->stream));
+    if (use_graph && n > 0 && !b->have_graph) {
+        cudaGraph_t g;
+        VP_BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+        vp_status st = batch_enqueue_step(b);
+        cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+        if (st != VP_OK) return st;
+        VP_BCUDA(b, e);
+        e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        VP_BCUDA(b, e);
+        b->have_graph = true;
+    }
+    for (int s = 0; s < n; ++s) {
+        if (use_graph) {
+            VP_BCUDA(b, cudaGraphLaunch(b->graph, b->stream));
+        } else {
+            vp_status st = batch_enqueue_step(b);
+            if (st != VP_OK) return st;
+        }
+    }
+    // host copies of the buffer parity follow the device ones
+    for (int k = 0; k < b->ninst; ++k) b->sims[k]->cur = (b->sims[k]->cur + n) & 1;
+    // the parity upload above reads host memory: complete it before the vector is reused
+    VP_BCUDA(b, cudaStreamSynchronize(b->stream));
+    return VP_OK;
+}
+
+vp_status vp_batch_sync(vp_batch *b)
+{
+    if (!b) return VP_ERR_ARG;
+    VP_BCUDA(b, cudaStreamSynchronize(b->stream));
+    return VP_OK;
+}
+
+void vp_batch_destroy(vp_batch *b)
+{
+    if (!b) return;
+    if (b->have_graph) cudaGraphExecDestroy(b->graph);
+    delete b;
+}
+
+const char *vp_batch_last_error(const vp_batch *b) { return b ? b->msg : "NULL batch"; }
+
+}  // extern "C"

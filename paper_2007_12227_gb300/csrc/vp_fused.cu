@@ -442,13 +442,14 @@ __device__ __forceinline__ void gal_rows(T *win, const WinGeom &W, T *dst, int L
 }
 
 // ---------------------------------------------------------------------------
+// One destination tile of one simulation (A may live in shared or global memory).
 template <typename T, int BASIS, bool GAL, bool UTERM>
-__global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const FusedArgs<T> A)
+__device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile,
+                                           unsigned char *smem_raw)
 {
     using TP = FTaps<T, BASIS>;
     constexpr int N = TP::N;
     constexpr int R = (BASIS == VP_BASIS_TENT) ? 1 : 2;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T *win = reinterpret_cast<T *>(smem_raw);
     T *gcol = win + (size_t)A.ws * (A.tp + 2 * A.Gp);   // [GRows][blockDim] column buffer (Galerkin)
     __shared__ int s_ia, s_ib, s_ja, s_jb;
@@ -459,7 +460,6 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const F
 
     const Geometry &g = A.g;
     const int nx = g.nx, np = g.np;
-    const int tile = blockIdx.x;
     const int tix = tile % A.ntx, tip = tile / A.ntx;
     const int X0 = tix * A.tx, P0 = tip * A.tp;
     const int TXe = min(A.tx, nx - X0), TPe = min(A.tp, np - P0);
@@ -748,6 +748,39 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const F
     }
 }
 
+template <typename T, int BASIS, bool GAL, bool UTERM>
+__global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const FusedArgs<T> A)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    fused_tile<T, BASIS, GAL, UTERM>(A, blockIdx.x, smem_raw);
+}
+
+// Persistent batched step: CTAs take (instance, tile) items from a counter; instance k
+// uses args[2 k + parity[k]] (parity = which buffer holds its current state).
+template <typename T, int BASIS, bool GAL, bool UTERM>
+__global__ void __launch_bounds__(kFusedMaxThreads, 2)
+    step_fused_batch_kernel(const FusedArgs<T> *__restrict__ args, const int *__restrict__ parity,
+                            const int2 *__restrict__ items, int nitems, int *counter)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(16) FusedArgs<T> sA;
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= nitems) break;
+        const int2 e = items[it];
+        const FusedArgs<T> *src = args + 2 * e.x + parity[e.x];
+        constexpr int nwords = sizeof(FusedArgs<T>) / 4;
+        for (int k = threadIdx.x; k < nwords; k += blockDim.x)
+            reinterpret_cast<int *>(&sA)[k] = reinterpret_cast<const int *>(src)[k];
+        __syncthreads();
+        fused_tile<T, BASIS, GAL, UTERM>(sA, e.y, smem_raw);
+        __syncthreads();
+    }
+}
+
 template <typename T>
 size_t fused_smem_bytes(int ws, int wh, int threads)
 {
@@ -808,6 +841,33 @@ cudaError_t launch_lambda_p_mul(const T *w, T *s, int nx, int np, cudaStream_t s
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_step_fused_batch(const FusedArgs<T> *args, const int *parity, const int2 *items,
+                                    int nitems, int *counter, int basis, int projection,
+                                    size_t smem, int threads, int grid, cudaStream_t s)
+{
+    const bool gal = basis == VP_BASIS_CUBIC_BSPLINE && projection == VP_PROJ_GALERKIN;
+#define VP_LAUNCH_BATCH(B, GL)                                                                \
+    do {                                                                                      \
+        auto k = step_fused_batch_kernel<T, B, GL, true>;                                     \
+        if (grid <= 0) /* set-up call: shared-memory attribute only (not capturable) */       \
+            return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                                        (int)smem);                                           \
+        k<<<grid, threads, smem, s>>>(args, parity, items, nitems, counter);                  \
+    } while (0)
+    if (basis == VP_BASIS_TENT) VP_LAUNCH_BATCH(VP_BASIS_TENT, false);
+    else if (!gal) VP_LAUNCH_BATCH(VP_BASIS_CUBIC_BSPLINE, false);
+    else VP_LAUNCH_BATCH(VP_BASIS_CUBIC_BSPLINE, true);
+#undef VP_LAUNCH_BATCH
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_step_fused_batch<float>(const FusedArgs<float> *, const int *, const int2 *,
+                                                    int, int *, int, int, size_t, int, int,
+                                                    cudaStream_t);
+template cudaError_t launch_step_fused_batch<double>(const FusedArgs<double> *, const int *,
+                                                     const int2 *, int, int *, int, int, size_t, int,
+                                                     int, cudaStream_t);
 template size_t fused_smem_bytes<float>(int, int, int);
 template size_t fused_smem_bytes<double>(int, int, int);
 template cudaError_t launch_step_fused<float>(const FusedArgs<float> &, int, cudaStream_t);

@@ -126,6 +126,20 @@ template <typename T>
 cudaError_t launch_step_fused(const FusedArgs<T> &a, int threads, cudaStream_t s);
 template <typename T>
 size_t fused_smem_bytes(int ws, int wh, int threads);
+template <typename T>
+cudaError_t launch_step_fused_batch(const FusedArgs<T> *args, const int *parity, const int2 *items,
+                                    int nitems, int *counter, int basis, int projection,
+                                    size_t smem, int threads, int grid, cudaStream_t s);
+
+// per-instance end-of-step work of a batch: FEL field update, or the step counter
+struct BatchFinal {
+    double *state;
+    const double *part;
+    double *hist;
+    int nparts, hist_cap, fel;
+    double dt;
+};
+cudaError_t launch_batch_finalize(const BatchFinal *fin, int ninst, int *parity, cudaStream_t s);
 constexpr int fused_halo(int precision) { return precision == VP_FP64 ? 28 : 14; }
 constexpr int kFusedMaxRow = 512; // longest window row one warp solves
 constexpr int kFusedMaxTileP = 256; // tallest tile of the fused kernel

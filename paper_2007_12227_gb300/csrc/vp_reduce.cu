@@ -58,8 +58,9 @@ __global__ void fel_partials_kernel(const T *__restrict__ w, int nx, int np,
     }
 }
 
-__global__ void fel_finalize_kernel(const double *__restrict__ part, int nparts, double *state,
-                                    double *hist, int hist_cap, double dt, int init)
+// FEL field update from per-block partial sums (run by one block)
+__device__ void fel_finalize_block(const double *__restrict__ part, int nparts, double *state,
+                                   double *hist, int hist_cap, double dt, int init)
 {
     __shared__ double s[3][kRedThreads];
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
@@ -107,6 +108,26 @@ __global__ void fel_finalize_kernel(const double *__restrict__ part, int nparts,
     }
     state[ST_STEP] = (double)(step + 1);
     state[ST_TAU] = (double)(step + 1) * dt;
+}
+
+__global__ void fel_finalize_kernel(const double *__restrict__ part, int nparts, double *state,
+                                    double *hist, int hist_cap, double dt, int init)
+{
+    fel_finalize_block(part, nparts, state, hist, hist_cap, dt, init);
+}
+
+// end of a batched step: block k finishes instance k and flips its buffer parity
+__global__ void batch_finalize_kernel(const BatchFinal *__restrict__ fin, int *parity)
+{
+    const BatchFinal f = fin[blockIdx.x];
+    if (f.fel) {
+        fel_finalize_block(f.part, f.nparts, f.state, f.hist, f.hist_cap, f.dt, 0);
+    } else if (threadIdx.x == 0) {
+        const double st = f.state[ST_STEP] + 1.0;
+        f.state[ST_STEP] = st;
+        f.state[ST_TAU] = st * f.dt;
+    }
+    if (threadIdx.x == 0) parity[blockIdx.x] ^= 1;
 }
 
 // plain step counter for non-FEL sims
@@ -225,6 +246,12 @@ cudaError_t launch_fel_finalize(const double *part, int nparts, double *state, d
                                 int hist_cap, double dt, int init, cudaStream_t s)
 {
     fel_finalize_kernel<<<1, kRedThreads, 0, s>>>(part, nparts, state, hist, hist_cap, dt, init);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch_finalize(const BatchFinal *fin, int ninst, int *parity, cudaStream_t s)
+{
+    batch_finalize_kernel<<<ninst, kRedThreads, 0, s>>>(fin, parity);
     return cudaGetLastError();
 }
 

@@ -52,6 +52,23 @@ class vp_moments_t(C.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class vp_server_opts(C.Structure):
+    _fields_ = [("budget_bytes", C.c_size_t), ("slice_steps", C.c_int32), ("max_active", C.c_int32),
+                ("stream", C.c_void_p)]
+
+
+class vp_request(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("grid", vp_grid), ("basis", C.c_int32), ("pusher", vp_pusher),
+                ("precision", C.c_int32), ("projection", C.c_int32), ("steps", C.c_int32),
+                ("keep_f", C.c_int32), ("f0", C.c_void_p), ("f0_dtype", C.c_int32)]
+
+
+class vp_result(C.Structure):
+    _fields_ = [("id", C.c_uint64), ("status", C.c_int32), ("batched", C.c_int32),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_finish", C.c_double),
+                ("moments", vp_moments_t)]
+
+
 _lib = None
 
 # (name, restype, argtypes) for every function of include/vlasov.h
@@ -72,6 +89,22 @@ _SIGNATURES = [
     ("vp_sync", C.c_int, [C.c_void_p]),
     ("vp_set_stream", C.c_int, [C.c_void_p, C.c_void_p]),
     ("vp_state_device", C.c_int, [C.c_void_p, C.POINTER(C.c_void_p)]),
+    ("vp_batch_workspace_size", C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_size_t)]),
+    ("vp_batch_create", C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p, C.c_void_p,
+                                  C.c_size_t, C.POINTER(C.c_void_p)]),
+    ("vp_batch_step", C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    ("vp_batch_sync", C.c_int, [C.c_void_p]),
+    ("vp_batch_destroy", None, [C.c_void_p]),
+    ("vp_batch_last_error", C.c_char_p, [C.c_void_p]),
+    ("vp_server_create", C.c_int, [C.POINTER(vp_server_opts), C.c_void_p, C.c_size_t,
+                                   C.POINTER(C.c_void_p)]),
+    ("vp_server_submit", C.c_int, [C.c_void_p, C.POINTER(vp_request)]),
+    ("vp_server_run", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    ("vp_server_poll", C.c_int, [C.c_void_p, C.POINTER(vp_result), C.c_int32, C.POINTER(C.c_int32)]),
+    ("vp_server_take_f", C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int32, C.c_size_t]),
+    ("vp_server_clock", C.c_double, []),
+    ("vp_server_destroy", None, [C.c_void_p]),
+    ("vp_server_last_error", C.c_char_p, [C.c_void_p]),
     ("vp_destroy", None, [C.c_void_p]),
     ("vp_last_error", C.c_char_p, [C.c_void_p]),
     ("vp_status_string", C.c_char_p, [C.c_int]),
@@ -217,6 +250,122 @@ class Sim:
     def close(self):
         if getattr(self, "h", None):
             lib().vp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several Sim objects advanced together by the batched one-pass kernel."""
+
+    def __init__(self, sims, stream=None, device="cuda"):
+        import torch
+        self.sims = list(sims)
+        if stream is None:
+            stream = self.sims[0].stream
+        self.stream = stream
+        arr = (C.c_void_p * len(self.sims))(*[s.h.value for s in self.sims])
+        self._arr = arr
+        n = C.c_size_t()
+        _check(lib().vp_batch_workspace_size(arr, len(self.sims), C.byref(n)))
+        self.workspace = torch.empty(n.value + 256, dtype=torch.uint8, device=device)
+        aligned = (self.workspace.data_ptr() + 255) // 256 * 256
+        h = C.c_void_p()
+        st = lib().vp_batch_create(arr, len(self.sims), C.c_void_p(stream.cuda_stream),
+                                   C.c_void_p(aligned), n.value, C.byref(h))
+        if st != VP_OK:
+            raise VlasovError(st, "vp_batch_create")
+        self.h = h
+
+    def step(self, n=1, use_graph=True):
+        st = lib().vp_batch_step(self.h, int(n), 1 if use_graph else 0)
+        if st != VP_OK:
+            raise VlasovError(st, lib().vp_batch_last_error(self.h).decode())
+
+    def sync(self):
+        st = lib().vp_batch_sync(self.h)
+        if st != VP_OK:
+            raise VlasovError(st, lib().vp_batch_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().vp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Continuous-batching request loop over a torch-allocated device arena."""
+
+    def __init__(self, arena_bytes, budget_bytes=0, slice_steps=0, max_active=0, stream=None,
+                 device="cuda"):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+        self.arena = torch.empty(arena_bytes + 256, dtype=torch.uint8, device=device)
+        aligned = (self.arena.data_ptr() + 255) // 256 * 256
+        self.opts = vp_server_opts(int(budget_bytes), int(slice_steps), int(max_active),
+                                   C.c_void_p(stream.cuda_stream))
+        h = C.c_void_p()
+        st = lib().vp_server_create(C.byref(self.opts), C.c_void_p(aligned), int(arena_bytes), C.byref(h))
+        if st != VP_OK:
+            raise VlasovError(st, "vp_server_create")
+        self.h = h
+        self._hold = {}
+
+    def _err(self, st):
+        if st != VP_OK:
+            raise VlasovError(st, lib().vp_server_last_error(self.h).decode())
+
+    def submit(self, rid, grid, basis, pusher, f0, steps, precision=VP_FP32,
+               projection=VP_PROJ_GALERKIN, keep_f=False):
+        a = np.ascontiguousarray(f0.reshape(grid.np, grid.nx))
+        dt = VP_FP64 if a.dtype == np.float64 else VP_FP32
+        if a.dtype not in (np.float32, np.float64):
+            a, dt = a.astype(np.float64), VP_FP64
+        req = vp_request(int(rid), make_grid(grid), int(basis), make_pusher(pusher), int(precision),
+                         int(projection), int(steps), 1 if keep_f else 0, a.ctypes.data, dt)
+        self._err(lib().vp_server_submit(self.h, C.byref(req)))
+
+    def run(self, rounds=1):
+        q, a = C.c_int32(), C.c_int32()
+        self._err(lib().vp_server_run(self.h, int(rounds), C.byref(q), C.byref(a)))
+        return q.value, a.value
+
+    def poll(self, max_results=4096):
+        buf = (vp_result * max_results)()
+        n = C.c_int32()
+        self._err(lib().vp_server_poll(self.h, buf, max_results, C.byref(n)))
+        out = []
+        for k in range(n.value):
+            r = buf[k]
+            out.append(dict(id=r.id, status=r.status, batched=r.batched, t_submit=r.t_submit,
+                            t_admit=r.t_admit, t_finish=r.t_finish, moments=r.moments.as_dict()))
+        return out
+
+    def take_f(self, rid, shape, dtype=np.float64):
+        out = np.empty(shape, dtype=dtype)
+        dt = VP_FP64 if out.dtype == np.float64 else VP_FP32
+        self._err(lib().vp_server_take_f(self.h, int(rid), out.ctypes.data_as(C.c_void_p), dt, out.size))
+        return out
+
+    @staticmethod
+    def clock():
+        return lib().vp_server_clock()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().vp_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

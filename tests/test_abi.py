@@ -48,14 +48,16 @@ def test_every_declared_function_is_exported_and_bound(lib):
 def test_struct_layouts_match_the_header(tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "vlasov.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(vp_grid), '
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(vp_grid), '
                    'sizeof(vp_pusher), sizeof(vp_opts), sizeof(vp_moments_t), '
-                   'offsetof(vp_moments_t, step)); return 0;}\n')
+                   'offsetof(vp_moments_t, step), sizeof(vp_server_opts), sizeof(vp_request), '
+                   'sizeof(vp_result), offsetof(vp_request, f0)); return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     want = [C.sizeof(V.vp_grid), C.sizeof(V.vp_pusher), C.sizeof(V.vp_opts),
-            C.sizeof(V.vp_moments_t), V.vp_moments_t.step.offset]
+            C.sizeof(V.vp_moments_t), V.vp_moments_t.step.offset, C.sizeof(V.vp_server_opts),
+            C.sizeof(V.vp_request), C.sizeof(V.vp_result), V.vp_request.f0.offset]
     assert got == want
 
 
@@ -135,3 +137,27 @@ def test_binding_fails_loudly_without_the_library(monkeypatch, tmp_path):
     monkeypatch.setattr(V, "_lib", None)
     with pytest.raises(RuntimeError):
         V.lib()
+
+
+def test_server_host_paths_without_a_gpu(lib):
+    """Create, queue an invalid request, report its status, destroy: no device work."""
+    buf = (C.c_char * 4096)()
+    base = (C.addressof(buf) + 255) // 256 * 256
+    o = V.vp_server_opts(1024, 0, 0, None)
+    h = C.c_void_p()
+    assert lib.vp_server_create(C.byref(o), C.c_void_p(base), 1024, C.byref(h)) == V.VP_OK
+    f0 = (C.c_float * 24)()
+    req = V.vp_request(11, V.vp_grid(3, 8, -3.14, 3.14, -1.0, 1.0), 1,
+                       V.vp_pusher(0, 1, 1.0, 1.0, 0.1, 0.0, 0.0), 0, 0, 5, 0,
+                       C.cast(f0, C.c_void_p), 0)
+    assert lib.vp_server_submit(h, C.byref(req)) == V.VP_OK
+    q, a = C.c_int32(), C.c_int32()
+    assert lib.vp_server_run(h, 3, C.byref(q), C.byref(a)) == V.VP_OK
+    assert q.value == 0 and a.value == 0
+    res = (V.vp_result * 4)()
+    n = C.c_int32()
+    assert lib.vp_server_poll(h, res, 4, C.byref(n)) == V.VP_OK
+    assert n.value == 1 and res[0].id == 11 and res[0].status == V.VP_ERR_ARG
+    bad = V.vp_request(12, V.vp_grid(8, 8, 0, 1, 0, 1), 1, V.vp_pusher(), 0, 0, -1, 0, None, 0)
+    assert lib.vp_server_submit(h, C.byref(bad)) == V.VP_ERR_ARG
+    lib.vp_server_destroy(h)
