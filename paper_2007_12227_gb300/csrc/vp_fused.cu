@@ -36,10 +36,11 @@
 namespace vp {
 namespace {
 
-// look-ahead / x-solve halo: |z|^14 = 1e-8 (FP32), |z|^28 = 1e-16 (FP64)
+// look-ahead / x-solve halo: |z|^16 = 7e-10 (FP32; also keeps stores 16-byte aligned),
+// |z|^28 = 1e-16 (FP64)
 template <typename T>
 struct Halo {
-    static constexpr int value = sizeof(T) == 4 ? 14 : 28;
+    static constexpr int value = sizeof(T) == 4 ? 16 : 28;
 };
 constexpr int kC = 16;              // rows per chunk of the p solve (multiple of 4)
 // rows of the per-thread column buffer: one chunk, or the look-ahead above the top row
@@ -189,6 +190,36 @@ template <typename T, int N, int DIR>
 __device__ __forceinline__ void ring_add(T *win, const WinGeom &W, Ring<T, N> &rg, int m, int n,
                                          const T *wx, const T *wy, double &lost)
 {
+    {
+        // common case for the whole warp: one row leaves the ring, nothing else changes
+        const int rl = DIR > 0 ? rg.nb : rg.nb + N - 1;
+        const bool fast = rg.live && n == rg.nb + DIR && m == rg.mref && rg.col_ok &&
+                          (unsigned)rl < (unsigned)W.WH;
+        if (__all_sync(__activemask(), fast)) {
+            T *p = win + rl * W.ws + rg.mref;
+            if (DIR > 0) {
+#pragma unroll
+                for (int a = 0; a < N; ++a) atomicAdd(p + a, rg.acc[0][a]);
+#pragma unroll
+                for (int b = 0; b < N - 1; ++b)
+#pragma unroll
+                    for (int a = 0; a < N; ++a) rg.acc[b][a] = rg.acc[b + 1][a] + wy[b] * wx[a];
+#pragma unroll
+                for (int a = 0; a < N; ++a) rg.acc[N - 1][a] = wy[N - 1] * wx[a];
+            } else {
+#pragma unroll
+                for (int a = 0; a < N; ++a) atomicAdd(p + a, rg.acc[N - 1][a]);
+#pragma unroll
+                for (int b = N - 1; b > 0; --b)
+#pragma unroll
+                    for (int a = 0; a < N; ++a) rg.acc[b][a] = rg.acc[b - 1][a] + wy[b] * wx[a];
+#pragma unroll
+                for (int a = 0; a < N; ++a) rg.acc[0][a] = wy[0] * wx[a];
+            }
+            rg.nb = n;
+            return;
+        }
+    }
     const bool step_ok = rg.live && n == rg.nb + DIR;
     if (step_ok && (m == rg.mref + 1 || m == rg.mref - 1)) {
         // the base column moved by one: flush the column that leaves, shift the rest
@@ -429,15 +460,37 @@ __device__ __forceinline__ void gal_rows(T *win, const WinGeom &W, T *dst, int L
         int per, base;
         solve_row_x<T, KX>(row, L, full, lane, v, per, base);
         __syncwarp();
+        // v - v is 0 for finite values and NaN otherwise
+        T chk = T(0);
+        T *dp = dst_row + base;
+        const bool inside = per == KX && base >= D && base + KX <= D + TXe;
+        if (sizeof(T) == 4 && KX % 4 == 0 && inside && ((reinterpret_cast<uintptr_t>(dp) & 15) == 0)) {
 #pragma unroll
-        for (int k = 0; k < KX; ++k) {
-            const int c = base + k;
-            if (k < per && c >= D && c < D + TXe) {
-                dst_row[c] = v[k];
-                bad |= !isfinite(v[k]);
-                if (want_part) row[c] = v[k];   // keep s for the column sums
+            for (int k = 0; k < KX; k += 4) {
+                float4 q;
+                q.x = (float)v[k];
+                q.y = (float)v[k + 1];
+                q.z = (float)v[k + 2];
+                q.w = (float)v[k + 3];
+                *reinterpret_cast<float4 *>(dp + k) = q;
+            }
+#pragma unroll
+            for (int k = 0; k < KX; ++k) chk += v[k] - v[k];
+            if (want_part)
+#pragma unroll
+                for (int k = 0; k < KX; ++k) row[base + k] = v[k];   // keep s for the column sums
+        } else {
+#pragma unroll
+            for (int k = 0; k < KX; ++k) {
+                const int c = base + k;
+                if (k < per && c >= D && c < D + TXe) {
+                    dst_row[c] = v[k];
+                    chk += v[k] - v[k];
+                    if (want_part) row[c] = v[k];   // keep s for the column sums
+                }
             }
         }
+        bad |= chk != T(0);
     }
 }
 
@@ -481,7 +534,12 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
     W.full = full;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
 
-    for (int k = tid; k < W.WH * W.ws; k += blockDim.x) win[k] = T(0);
+    {
+        const int nvec = (int)(((size_t)W.WH * W.ws * sizeof(T)) / 16);
+        uint4 *w4 = reinterpret_cast<uint4 *>(win);
+        for (int k = tid; k < nvec; k += blockDim.x) w4[k] = make_uint4(0, 0, 0, 0);
+        for (int k = nvec * (16 / (int)sizeof(T)) + tid; k < W.WH * W.ws; k += blockDim.x) win[k] = T(0);
+    }
     for (int k = tid; k <= kPivots; k += blockDim.x) {
         piv_cp[k] = (T)A.piv[2 * k];
         piv_ib[k] = (T)A.piv[2 * k + 1];
@@ -642,24 +700,45 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
                         for (rr = top; rr > jb; --rr) uv = gc[(rr - jb - 1) * nth] - piv_cp[min(rr, kPivots)] * uv;
                     }
                 }
+                const T ib_inf = piv_ib[kPivots], cp_inf = piv_cp[kPivots];
+                const T ib6_inf = sixth * ib_inf;
                 for (int c_hi = jb; c_hi >= ja; c_hi -= kC) {
                     const int c_lo = max(ja, c_hi - kC + 1);
                     int rr = max(0, c_lo - kHalo);
                     const T *sp = src + (size_t)rr * nx;
                     T gv = T(0);
+                    if (c_lo - kHalo > kPivots) {
+                        // far from the first row the pivots have their limits
 #pragma unroll 4
-                    for (; rr < c_lo; ++rr, sp += nx) gv = (*sp - sixth * gv) * piv_ib[min(rr, kPivots)];
+                        for (; rr < c_lo; ++rr, sp += nx) gv = *sp * ib_inf - ib6_inf * gv;
 #pragma unroll 4
-                    for (; rr <= c_hi; ++rr, sp += nx) {
-                        gv = (*sp - sixth * gv) * piv_ib[min(rr, kPivots)];
-                        gc[(rr - c_lo) * nth] = gv;
+                        for (; rr <= c_hi; ++rr, sp += nx) {
+                            gv = *sp * ib_inf - ib6_inf * gv;
+                            gc[(rr - c_lo) * nth] = gv;
+                        }
+                    } else {
+                        for (; rr < c_lo; ++rr, sp += nx) gv = (*sp - sixth * gv) * piv_ib[min(rr, kPivots)];
+                        for (; rr <= c_hi; ++rr, sp += nx) {
+                            gv = (*sp - sixth * gv) * piv_ib[min(rr, kPivots)];
+                            gc[(rr - c_lo) * nth] = gv;
+                        }
                     }
+                    const RowEntry<T> *rp = A.row + c_hi;
+                    if (c_lo > kPivots) {
 #pragma unroll 2
-                    for (int r = c_hi; r >= c_lo; --r) {
-                        uv = gc[(r - c_lo) * nth] - piv_cp[min(r, kPivots)] * uv;
-                        int m, n;
-                        node_taps<T, BASIS, UTERM>(cc, A.row[r], colrel, r - W.WP0, uv, m, n, wx, wy);
-                        ring_add<T, N, -1>(win, W, rg, m, n, wx, wy, lost);
+                        for (int r = c_hi; r >= c_lo; --r, --rp) {
+                            uv = gc[(r - c_lo) * nth] - cp_inf * uv;
+                            int m, n;
+                            node_taps<T, BASIS, UTERM>(cc, *rp, colrel, r - W.WP0, uv, m, n, wx, wy);
+                            ring_add<T, N, -1>(win, W, rg, m, n, wx, wy, lost);
+                        }
+                    } else {
+                        for (int r = c_hi; r >= c_lo; --r, --rp) {
+                            uv = gc[(r - c_lo) * nth] - piv_cp[min(r, kPivots)] * uv;
+                            int m, n;
+                            node_taps<T, BASIS, UTERM>(cc, *rp, colrel, r - W.WP0, uv, m, n, wx, wy);
+                            ring_add<T, N, -1>(win, W, rg, m, n, wx, wy, lost);
+                        }
                     }
                 }
                 ring_final<T, N>(win, W, rg, lost);
@@ -669,6 +748,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
     __syncthreads();
 
     // ---- window rows beyond the open momentum edge: lost weight of the own columns
+    if (W.WP0 < 0 || W.WP0 + W.WH > np)
     for (int rr = 0; rr < W.WH; ++rr) {
         const int grow = rr + W.WP0;
         if (grow >= 0 && grow < np) continue;

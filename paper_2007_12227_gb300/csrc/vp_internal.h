@@ -29,7 +29,7 @@ struct ColEntry {
 };
 
 template <typename T>
-struct RowEntry {
+struct __align__(16) RowEntry {   // padded so that a row loads with two vector loads
     int ui, vi;
     T uf, vf, sy, cy;
 };
@@ -140,7 +140,7 @@ struct BatchFinal {
     double dt;
 };
 cudaError_t launch_batch_finalize(const BatchFinal *fin, int ninst, int *parity, cudaStream_t s);
-constexpr int fused_halo(int precision) { return precision == VP_FP64 ? 28 : 14; }
+constexpr int fused_halo(int precision) { return precision == VP_FP64 ? 28 : 16; }
 constexpr int kFusedMaxRow = 512; // longest window row one warp solves
 constexpr int kFusedMaxTileP = 256; // tallest tile of the fused kernel
 template <typename T>

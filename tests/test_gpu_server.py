@@ -73,12 +73,12 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
 
 def test_budget_admission_is_fifo_and_bounded():
     stream = torch.cuda.Stream()
-    reqs = small_trace(10)
-    # room for only a few requests at a time
-    one = max(V.vp_workspace_size(V.make_grid(r.workload.grid), r.workload.basis,
-                                  V.make_pusher(r.workload.pusher),
-                                  V.vp_opts(0, 0, 0, 0, 0, 0, None)) for r in reqs)
-    srv = V.Server(4 * one, budget_bytes=3 * one, slice_steps=5, stream=stream)
+    # ten equal requests; the budget holds three of them (the batch tables also take room)
+    base = I.pendulum_8192_fp32_cubic(300, 300, steps=12)
+    reqs = [I.Request(k, 0.0, base) for k in range(10)]
+    one = V.vp_workspace_size(V.make_grid(base.grid), base.basis, V.make_pusher(base.pusher),
+                              V.vp_opts(0, 0, 0, 0, 0, 0, None))
+    srv = V.Server(4 * one, budget_bytes=3 * one + 4096, slice_steps=5, stream=stream)
     for r in reqs:
         srv.submit(r.rid, r.workload.grid, r.workload.basis, r.workload.pusher,
                    I.make_f0(r.workload).astype(np.float32), r.workload.steps)
