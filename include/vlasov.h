@@ -170,6 +170,22 @@ vp_status vp_field_history(vp_sim *sim, double *re_im, size_t max_entries, size_
 /* Synchronise the sim's stream and report device-side error flags. */
 vp_status vp_sync(vp_sim *sim);
 
+/* Moments of a weight array the caller already holds on the device, with no
+ * device allocation: for callers that cannot allocate when they need the
+ * diagnostics (during CUDA-graph capture, under a framework allocator that owns
+ * the device, in time-critical loops). The paper has no counterpart; it gives
+ * the same FP64 reductions as vp_moments. w: device pointer, [np][nx] of dtype
+ * VP_FP32 or VP_FP64; lost_mass and a_re_im (host, may be NULL) are copied into
+ * the result; stream: cudaStream_t (NULL = default); synchronises that stream.
+ * The partial sums live in one static device array of this library (about
+ * 427 KB per GPU, held until exit); meshes above 2^26 nodes are rejected with
+ * VP_ERR_UNSUPPORTED. The first call on a device looks up that array's device
+ * address, so make it before any stream capture. Calls share the array:
+ * calls that overlap on the GPU race. */
+vp_status vp_moments_static(const void *w, int32_t dtype, const vp_grid *grid,
+                            const vp_pusher *pusher, double lost_mass, const double *a_re_im,
+                            vp_moments_t *out, void *stream);
+
 /* Redirect later work to another stream (no synchronisation is implied). */
 vp_status vp_set_stream(vp_sim *sim, void *stream);
 

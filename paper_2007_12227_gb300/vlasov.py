@@ -105,6 +105,9 @@ _SIGNATURES = [
     ("vp_server_clock", C.c_double, []),
     ("vp_server_destroy", None, [C.c_void_p]),
     ("vp_server_last_error", C.c_char_p, [C.c_void_p]),
+    ("vp_moments_static", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(vp_grid), C.POINTER(vp_pusher),
+                                    C.c_double, C.POINTER(C.c_double), C.POINTER(vp_moments_t),
+                                    C.c_void_p]),
     ("vp_destroy", None, [C.c_void_p]),
     ("vp_last_error", C.c_char_p, [C.c_void_p]),
     ("vp_status_string", C.c_char_p, [C.c_int]),
