@@ -28,8 +28,8 @@ constexpr int kMoutLen = 32;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t f0, f1, tmp, col, row, rowb, vcb, csx, ucol, vcol, piv, sigma, state, hist, lost, part,
-        mpart, mout, err, total;
+    size_t f0, f1, tmp, col, row, rowb, vcb, rowbf, vcbf, csx, ucol, vcol, piv, sigma, state, hist,
+        lost, part, mpart, mout, err, total;
 };
 
 struct Plan {
@@ -154,13 +154,16 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
         const int WW = full ? grid->nx + 2 * G : ftx + 2 * halo + 2 * G;
         const int ws = (WW + 31) / 32 * 32 + 1;
         const int wsrc = (full ? grid->nx : ftx + 2 * halo) + 2 * R + 8;
-        const int threads = std::min(kFusedMaxThreads, (wsrc + 31) / 32 * 32);
-        // two CTAs per SM when the window allows it
+        // two CTAs per SM (up to 320 threads) unless the tile is wide: then one CTA of up
+        // to 576 threads per SM
+        const bool wide = (wsrc + 31) / 32 * 32 > kFusedThreads2;
+        const int threads = std::min(wide ? kFusedMaxThreads : kFusedThreads2, (wsrc + 31) / 32 * 32);
+        const size_t cap = wide ? (size_t)200 * 1024 : (size_t)112 * 1024;
         auto smem_of = [&](int tp_) {
             return sz == 8 ? fused_smem_bytes<double>(ws, tp_ + 2 * Gp, threads)
                            : fused_smem_bytes<float>(ws, tp_ + 2 * Gp, threads);
         };
-        while (smem_of(ftp) > 112 * 1024 && ftp > 8) ftp /= 2;
+        while (smem_of(ftp) > cap && ftp > 8) ftp /= 2;
         const size_t smem = smem_of(ftp);
         const bool ok = !wide_rotation && smem <= kMaxSmem && (full || WW < grid->nx) && ftx >= 1;
         if (ok) {
@@ -228,6 +231,8 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     L.row = take(grid->np * rowsz);
     L.rowb = take(grid->np * sizeof(RowBound));
     L.vcb = take(P->nblk * 2 * sizeof(double));
+    L.rowbf = take(grid->np * sizeof(float4));
+    L.vcbf = take(P->nblk * sizeof(float2));
     L.csx = take(grid->nx * sizeof(double2));
     L.ucol = take(grid->nx * sizeof(double));
     L.vcol = take(grid->nx * sizeof(double));
@@ -312,6 +317,8 @@ FusedArgs<T> fused_args(vp_sim *s, const void *src, void *dst)
     a.row = s->ptr<RowEntry<T>>(P.L.row);
     a.rowb = s->ptr<RowBound>(P.L.rowb);
     a.vcb = s->ptr<double>(P.L.vcb);
+    a.rowbf = s->ptr<float4>(P.L.rowbf);
+    a.vcbf = s->ptr<float2>(P.L.vcbf);
     a.state = s->ptr<double>(P.L.state);
     a.piv = s->ptr<double>(P.L.piv);
     a.sigma = s->ptr<double>(P.L.sigma);
@@ -578,6 +585,19 @@ vp_status vp_create(const vp_grid *grid, int32_t basis, const vp_pusher *pusher,
         }
         for (int j = g.np - 2; j >= 0; --j) sigma[j] -= cpv[j] * sigma[j + 1];
     }
+    // FP32 copies of the bound tables for the one-pass kernel's tile bounds
+    std::vector<float4> rowbf(g.np);
+    for (int j = 0; j < g.np; ++j)
+        rowbf[j] = make_float4((float)rowb[j].u, (float)rowb[j].v, (float)rowb[j].y, 0.f);
+    std::vector<float2> vcbf(P.nblk);
+    for (int b = 0; b < P.nblk; ++b) vcbf[b] = make_float2((float)vcb[2 * b], (float)vcb[2 * b + 1]);
+    e = cudaMemcpyAsync(s->ws + P.L.rowbf, rowbf.data(), rowbf.size() * sizeof(float4),
+                        cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(s->ws + P.L.vcbf, vcbf.data(), vcbf.size() * sizeof(float2),
+                            cudaMemcpyHostToDevice, s->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cleanup(cuda_fail(nullptr, e, "bound table upload"));
     e = cudaMemcpyAsync(s->ws + P.L.sigma, sigma.data(), sigma.size() * sizeof(double),
                         cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);

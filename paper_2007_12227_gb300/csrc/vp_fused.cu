@@ -107,6 +107,27 @@ __device__ __forceinline__ double zpow<double>(int n)
     return (n & 1) ? -m : m;
 }
 
+// range of sin over [lo, hi] in FP32 (|lo|, |hi| < 1e3), widened by 1e-4
+__device__ void sin_range32(float lo, float hi, float &smin, float &smax)
+{
+    const float twopi = 6.28318530717958647692f;
+    if (hi - lo >= twopi - 1e-4f) {
+        smin = -1.f;
+        smax = 1.f;
+        return;
+    }
+    const float k = floorf(lo / twopi);
+    const float a = lo - k * twopi, b = hi - k * twopi;
+    const float sa = sinf(a), sb = sinf(b);
+    smin = fminf(sa, sb) - 1e-4f;
+    smax = fmaxf(sa, sb) + 1e-4f;
+    const float h1 = 1.57079632679f, h3 = 4.71238898038f;
+    if ((a <= h1 + 1e-4f && h1 - 1e-4f <= b) || (a <= h1 + twopi + 1e-4f && h1 + twopi - 1e-4f <= b))
+        smax = 1.f;
+    if ((a <= h3 + 1e-4f && h3 - 1e-4f <= b) || (a <= h3 + twopi + 1e-4f && h3 + twopi - 1e-4f <= b))
+        smin = -1.f;
+}
+
 // range of sin over [lo, hi]: FP64 reduction, FP32 evaluation, 1e-5 slack
 __device__ void sin_range_f(double lo, double hi, float &smin, float &smax)
 {
@@ -561,65 +582,71 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
     }
     __syncthreads();
 
-    // ---- bound the source nodes whose footprint can reach the widened tile
+    // ---- bound the source nodes whose footprint can reach the widened tile (FP32 with
+    //      slack: every magnitude here is below 1e5 cells, where FP32 is exact to 1e-2)
     {
-        const double SL = 0.02;   // cells; covers rounding of the FP32 push
-        const double EU = fabs(g.KU) * M, EV = fabs(g.KV) * M;
-        const double vd_min = g.vc_min + g.vr_min - EV, vd_max = g.vc_max + g.vr_max + EV;
+        const float SL = 0.05f;
+        const float Mf = (float)M, phif = (float)phi;
+        const float EU = fabsf((float)g.KU) * Mf, EV = fabsf((float)g.KV) * Mf;
+        const float KVM = (float)g.KV * Mf;
+        const float vcmin = (float)g.vc_min, vcmax = (float)g.vc_max;
+        const float ucmin = (float)g.uc_min, ucmax = (float)g.uc_max;
+        const float vd_min = vcmin + (float)g.vr_min - EV, vd_max = vcmax + (float)g.vr_max + EV;
+        const float x0f = (float)g.x0, hxf = (float)g.hx, padf = (float)g.a_pad;
         const bool edge_lo = P0 == 0, edge_hi = P0 + TPe == np;
-        const int jlo = edge_lo ? 0 : max(0, (int)floor(P0 - R - vd_max - SL));
-        const int jhi = edge_hi ? np - 1 : min(np - 1, (int)ceil(P0 + TPe - 1 + R - vd_min + SL));
-        const double acc_lo = edge_lo ? -1e300 : (double)(P0 - R);
-        const double acc_hi = edge_hi ? 1e300 : (double)(P0 + TPe - 1 + R);
+        const int jlo = edge_lo ? 0 : max(0, (int)floorf((float)(P0 - R) - vd_max - SL));
+        const int jhi = edge_hi ? np - 1 : min(np - 1, (int)ceilf((float)(P0 + TPe - 1 + R) - vd_min + SL));
+        const float acc_lo = edge_lo ? -1e30f : (float)(P0 - R);
+        const float acc_hi = edge_hi ? 1e30f : (float)(P0 + TPe - 1 + R);
         int my_ia = 0x7fffffff, my_ib = -0x7fffffff, my_ja = 0x7fffffff, my_jb = -0x7fffffff;
         for (int j = jlo + tid; j <= jhi; j += blockDim.x) {
-            const RowBound rb = A.rowb[j];
-            long ia, ib;
-            double vcl = g.vc_min, vch = g.vc_max;
+            const float4 rb = A.rowbf[j];   // u, v, y
+            int ia, ib;
+            float vcl = vcmin, vch = vcmax;
             float smin = -1.f, smax = 1.f;
             if (full) {
                 ia = 0;
                 ib = nx - 1;
             } else {
-                ia = (long)floor(X0 - D - R - rb.u - EU - g.uc_max - SL);
-                ib = (long)ceil(X0 + TXe + D - 1 + R - rb.u + EU - g.uc_min + SL);
-                const long width = ib - ia + 1;
+                ia = (int)floorf((float)(X0 - D - R) - rb.x - EU - ucmax - SL);
+                ib = (int)ceilf((float)(X0 + TXe + D - 1 + R) - rb.x + EU - ucmin + SL);
+                const int width = ib - ia + 1;
                 if (width < nx - 2 * kColBlock) {
-                    vcl = 1e300;
-                    vch = -1e300;
-                    const int start = imod((int)(ia % nx), nx);
+                    vcl = 1e30f;
+                    vch = -1e30f;
+                    const int start = imod(ia, nx);
                     int seg_lo[2], seg_hi[2], nseg = 1;
                     if (start + width <= nx) {
                         seg_lo[0] = start;
-                        seg_hi[0] = (int)(start + width - 1);
+                        seg_hi[0] = start + width - 1;
                     } else {
                         seg_lo[0] = start;
                         seg_hi[0] = nx - 1;
                         seg_lo[1] = 0;
-                        seg_hi[1] = (int)(start + width - 1 - nx);
+                        seg_hi[1] = start + width - 1 - nx;
                         nseg = 2;
                     }
                     for (int sg = 0; sg < nseg; ++sg)
-                        for (int b = seg_lo[sg] / kColBlock; b <= seg_hi[sg] / kColBlock; ++b) {
-                            vcl = fmin(vcl, A.vcb[2 * b]);
-                            vch = fmax(vch, A.vcb[2 * b + 1]);
+                        for (int bq = seg_lo[sg] / kColBlock; bq <= seg_hi[sg] / kColBlock; ++bq) {
+                            const float2 vb = A.vcbf[bq];
+                            vcl = fminf(vcl, vb.x);
+                            vch = fmaxf(vch, vb.y);
                         }
-                    if (EV > 0.0)
-                        sin_range_f(g.x0 + ia * g.hx - g.a_pad + rb.y + phi,
-                                    g.x0 + ib * g.hx + g.a_pad + rb.y + phi, smin, smax);
+                    if (EV > 0.f)
+                        sin_range32(x0f + ia * hxf - padf + rb.z + phif, x0f + ib * hxf + padf + rb.z + phif,
+                                    smin, smax);
                 }
             }
-            double tlo = 0.0, thi = 0.0;
-            if (EV > 0.0) {
-                const double k = g.KV * M;
-                tlo = fmin(k * smin, k * smax);
-                thi = fmax(k * smin, k * smax);
+            float tlo = 0.f, thi = 0.f;
+            if (EV > 0.f) {
+                tlo = fminf(KVM * smin, KVM * smax);
+                thi = fmaxf(KVM * smin, KVM * smax);
             }
-            const double vlo = j + rb.v + vcl + tlo - SL;
-            const double vhi = j + rb.v + vch + thi + SL;
+            const float vlo = (float)j + rb.y + vcl + tlo - SL;
+            const float vhi = (float)j + rb.y + vch + thi + SL;
             if (vhi > acc_lo && vlo < acc_hi) {
-                my_ia = min(my_ia, (int)ia);
-                my_ib = max(my_ib, (int)ib);
+                my_ia = min(my_ia, ia);
+                my_ib = max(my_ib, ib);
                 my_ja = min(my_ja, j);
                 my_jb = max(my_jb, j);
             }
@@ -828,8 +855,9 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
     }
 }
 
-template <typename T, int BASIS, bool GAL, bool UTERM>
-__global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const FusedArgs<T> A)
+template <typename T, int BASIS, bool GAL, bool UTERM, int MINB>
+__global__ void __launch_bounds__(MINB == 1 ? kFusedMaxThreads : kFusedThreads2, MINB)
+    step_fused_kernel(const FusedArgs<T> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     fused_tile<T, BASIS, GAL, UTERM>(A, blockIdx.x, smem_raw);
@@ -837,8 +865,8 @@ __global__ void __launch_bounds__(kFusedMaxThreads, 2) step_fused_kernel(const F
 
 // Persistent batched step: CTAs take (instance, tile) items from a counter; instance k
 // uses args[2 k + parity[k]] (parity = which buffer holds its current state).
-template <typename T, int BASIS, bool GAL, bool UTERM>
-__global__ void __launch_bounds__(kFusedMaxThreads, 2)
+template <typename T, int BASIS, bool GAL, bool UTERM, int MINB>
+__global__ void __launch_bounds__(MINB == 1 ? kFusedMaxThreads : kFusedThreads2, MINB)
     step_fused_batch_kernel(const FusedArgs<T> *__restrict__ args, const int *__restrict__ parity,
                             const int2 *__restrict__ items, int nitems, int *counter)
 {
@@ -877,7 +905,8 @@ cudaError_t launch_step_fused(const FusedArgs<T> &a, int threads, cudaStream_t s
     const bool uterm = a.g.kind == VP_PUSH_FEL_DKD;
 #define VP_LAUNCH_FUSED(B, GL, UT)                                                            \
     do {                                                                                      \
-        auto k = step_fused_kernel<T, B, GL, UT>;                                             \
+        auto k = threads > kFusedThreads2 ? step_fused_kernel<T, B, GL, UT, 1>                 \
+                                          : step_fused_kernel<T, B, GL, UT, 2>;                \
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                                              (int)smem);                                      \
         if (e != cudaSuccess) return e;                                                       \
@@ -929,7 +958,8 @@ cudaError_t launch_step_fused_batch(const FusedArgs<T> *args, const int *parity,
     const bool gal = basis == VP_BASIS_CUBIC_BSPLINE && projection == VP_PROJ_GALERKIN;
 #define VP_LAUNCH_BATCH(B, GL)                                                                \
     do {                                                                                      \
-        auto k = step_fused_batch_kernel<T, B, GL, true>;                                     \
+        auto k = threads > kFusedThreads2 ? step_fused_batch_kernel<T, B, GL, true, 1>         \
+                                          : step_fused_batch_kernel<T, B, GL, true, 2>;        \
         if (grid <= 0) /* set-up call: shared-memory attribute only (not capturable) */       \
             return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
                                         (int)smem);                                           \

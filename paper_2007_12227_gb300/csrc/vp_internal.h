@@ -86,7 +86,8 @@ struct StepArgs {
 };
 
 // One-pass step kernel (vp_fused.cu): see the description there.
-constexpr int kFusedMaxThreads = 320;
+constexpr int kFusedMaxThreads = 576;   // one CTA per SM (wide tiles)
+constexpr int kFusedThreads2 = 320;     // two CTAs per SM
 
 template <typename T>
 struct FusedArgs {
@@ -96,6 +97,8 @@ struct FusedArgs {
     const RowEntry<T> *row;
     const RowBound *rowb;
     const double *vcb;
+    const float4 *rowbf;    // FP32 copy of rowb: u, v, y (tile bounds)
+    const float2 *vcbf;     // FP32 copy of vcb
     const double *state;
     const double *piv;      // Thomas pivots of tridiag(1/6, 2/3, 1/6)
     const double *sigma;    // column sums of Lambda_p^{-1} (FEL partial sums in Galerkin mode)
