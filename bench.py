@@ -33,6 +33,9 @@ from paper_2007_12227_gb300 import inputs as I  # noqa: E402
 METRIC = "phase-space node-updates/s (push+deposit) and HBM GB/s vs peak; batched/served vs plain"
 UNIT = "node-updates/s"
 FALLBACK_HBM_GBS = 6800.0
+# sources of the one-pass step kernel: the committed ncu traffic applies only to these bytes
+FUSED_SOURCES = ["paper_2007_12227_gb300/csrc/vp_fused.cu", "paper_2007_12227_gb300/csrc/vp_internal.h",
+                 "paper_2007_12227_gb300/csrc/vp_sum.cuh"]
 
 
 def parse():
@@ -329,9 +332,7 @@ def main():
     peak, peak_kind = peaks()
     alg_bytes = bytes_per_node[names[dom]] * N
     achieved = alg_bytes / (phase_ms[dom] * 1e-3) / 1e9
-    kernel_files = {"push_deposit": ("step_tiled_pendulum_8192.md",
-                                     ["paper_2007_12227_gb300/csrc/vp_step.cu",
-                                      "paper_2007_12227_gb300/csrc/vp_internal.h"]),
+    kernel_files = {"push_deposit": ("step_fused_pendulum_8192.md", FUSED_SOURCES),
                     "lambda_inv_x": ("filter_x_pendulum_8192.md",
                                      ["paper_2007_12227_gb300/csrc/vp_filter.cu"]),
                     "lambda_inv_p": ("filter_p_pendulum_8192.md",

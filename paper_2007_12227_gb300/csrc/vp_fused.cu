@@ -370,14 +370,20 @@ __device__ __forceinline__ void node_taps(const ColC<T> &c, const RowEntry<T> &r
 // shared memory, by one warp. Returns each lane's elements base .. base + per - 1 in v.
 // cyclic: the row is one whole period; else the row is padded by the halo on both
 // sides and the recurrences start from zero at its ends (truncation |z|^halo).
+// padded staging layout of a row: element c at c + c / 8, so that lanes reading
+// contiguous chunks of 8 hit distinct shared-memory banks
+__device__ __forceinline__ int padc(int c) { return c + (c >> 3); }
+
 template <typename T, int kXMax>
-__device__ void solve_row_x(const T *row, int L, bool cyclic, int lane, T *v, int &per, int &base)
+__device__ void solve_row_x(const T *row, int L, bool cyclic, int lane, T *v, int &per, int &base,
+                            bool padded)
 {
     per = (L + 31) / 32;
     base = lane * per;
     const T z = (T)-0.26794919243112270647;
 #pragma unroll
-    for (int k = 0; k < kXMax; ++k) v[k] = (k < per && base + k < L) ? row[base + k] : T(0);
+    for (int k = 0; k < kXMax; ++k)
+        v[k] = (k < per && base + k < L) ? row[padded ? padc(base + k) : base + k] : T(0);
     const T zper = zpow<T>(per);
     // causal y_i = x_i + z y_{i-1}: lane-local sweep, then carries by a warp scan
     T y = T(0);
@@ -472,14 +478,25 @@ __device__ void solve_row_x(const T *row, int L, bool cyclic, int lane, T *v, in
 template <typename T, int KX>
 __device__ __forceinline__ void gal_rows(T *win, const WinGeom &W, T *dst, int L, bool full, int D,
                                          int G, int Gp, int TXe, int TPe, int P0, int X0, int nx,
-                                         bool want_part, int warp, int nwarps, int lane, bool &bad)
+                                         bool want_part, int warp, int nwarps, int lane, bool &bad,
+                                         T *stage_all, int stage_len)
 {
+    // per-warp padded copy of the row (conflict-free reads of contiguous chunks)
+    const int plen = padc(L) + 8;
+    const bool use_stage = stage_all != nullptr && (size_t)nwarps * plen <= (size_t)stage_len;
+    T *stage = use_stage ? stage_all + (size_t)warp * plen : nullptr;
     for (int rr = warp; rr < TPe; rr += nwarps) {
         T *row = win + (size_t)(rr + Gp) * W.ws + G;
         T *dst_row = dst + (size_t)(P0 + rr) * nx + X0 - D;
         T v[KX];
         int per, base;
-        solve_row_x<T, KX>(row, L, full, lane, v, per, base);
+        if (use_stage) {
+            for (int c = lane; c < L; c += 32) stage[padc(c)] = row[c];
+            __syncwarp();
+            solve_row_x<T, KX>(stage, L, full, lane, v, per, base, true);
+        } else {
+            solve_row_x<T, KX>(row, L, full, lane, v, per, base, false);
+        }
         __syncwarp();
         // v - v is 0 for finite values and NaN otherwise
         T chk = T(0);
@@ -802,10 +819,10 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
         const int L = full ? nx : TXe + 2 * D;
         if (L <= 256)
             gal_rows<T, 8>(win, W, A.dst, L, full, D, G, Gp, TXe, TPe, P0, X0, nx, want_part, warp,
-                           nwarps, lane, bad);
+                           nwarps, lane, bad, gcol, GRows<T>::value * blockDim.x);
         else
             gal_rows<T, kXBig>(win, W, A.dst, L, full, D, G, Gp, TXe, TPe, P0, X0, nx, want_part,
-                               warp, nwarps, lane, bad);
+                               warp, nwarps, lane, bad, gcol, GRows<T>::value * blockDim.x);
     } else {
         for (int k = tid; k < TXe * TPe; k += blockDim.x) {
             const int rr = k / TXe, c = k - rr * TXe;
