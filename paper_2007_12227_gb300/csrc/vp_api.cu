@@ -236,7 +236,7 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     L.csx = take(grid->nx * sizeof(double2));
     L.ucol = take(grid->nx * sizeof(double));
     L.vcol = take(grid->nx * sizeof(double));
-    L.piv = take((2 * kPivots + 2) * sizeof(double));
+    L.piv = take(kPivTable * sizeof(double));
     L.sigma = take(grid->np * sizeof(double));
     L.state = take(ST_NSTATE * sizeof(double));
     L.hist = take((size_t)P->hist_cap * 2 * sizeof(double));
@@ -280,6 +280,27 @@ vp_status cuda_fail(vp_sim *s, cudaError_t e, const char *what)
         cudaError_t e_ = (__VA_ARGS__);                                \
         if (e_ != cudaSuccess) return cuda_fail(sim, e_, #__VA_ARGS__); \
     } while (0)
+
+// FP32 scale applied after the Lambda_x recursions. In exact arithmetic the x recursions
+// times -6z and the p recursions with the limit pivots each leave a constant field unchanged.
+// With the FP32 pole and pivots a step of the two would scale it by about 1 - 7e-8, and such
+// a bias compounds from step to step into a mass drift (about 1.4e-4 after 2000 steps), far
+// above the rounding noise. So the scale is (1 - z)^2 / g_p, z the FP32 pole and g_p the DC
+// gain of the p recursion with the FP32 constants as the kernel forms them (ib6: the rounded
+// product (1/6) ib of the one-pass kernel, else the exact product), kept as hi + lo floats.
+void unit_gain_scale(double ib, double cp, bool rounded_ib6, double *hi, double *lo)
+{
+    const float zf = (float)-0.26794919243112270647;
+    const float ibf = (float)ib, cpf = (float)cp;
+    const float sixth = 1.0f / 6.0f;
+    const float ib6f = sixth * ibf;
+    const double ib6 = rounded_ib6 ? (double)ib6f : (double)sixth * (double)ibf;
+    const double gp = (double)ibf / ((1.0 + ib6) * (1.0 + (double)cpf));
+    const double c = (1.0 - (double)zf) * (1.0 - (double)zf) / gp;
+    const float h = (float)c;
+    *hi = (double)h;
+    *lo = (double)(float)(c - (double)h);
+}
 
 template <typename T>
 StepArgs<T> step_args(vp_sim *s, const void *src, void *dst)
@@ -396,8 +417,8 @@ vp_status do_steps(vp_sim *s, int n, cudaEvent_t *ev = nullptr)
             nparts = P.ntx * P.ntp;
         } else if (P.galerkin) {
             T *tmp = s->ptr<T>(P.L.tmp);
-            VP_CUDA(s, launch_filter_x<T>(static_cast<const T *>(dst), tmp, P.g.nx, P.g.np, err,
-                                          s->stream));
+            VP_CUDA(s, launch_filter_x<T>(static_cast<const T *>(dst), tmp, P.g.nx, P.g.np,
+                                          s->ptr<double>(P.L.piv), err, s->stream));
             if (e) VP_CUDA(s, cudaEventRecord(e[2], s->stream));
             VP_CUDA(s, launch_filter_p<T>(tmp, static_cast<T *>(dst), P.g.nx, P.g.np,
                                           s->ptr<double>(P.L.piv), s->ptr<double2>(P.L.csx), part,
@@ -560,7 +581,7 @@ vp_status vp_create(const vp_grid *grid, int32_t basis, const vp_pusher *pusher,
         vcb[2 * b + 1] = hi;
     }
     // Thomas pivots of tridiag(1/6, 2/3, 1/6) from the first row, and their limits
-    std::vector<double> piv(2 * kPivots + 2);
+    std::vector<double> piv(kPivTable, 0.0);
     double cprev = 0.0;
     for (int r = 0; r < kPivots; ++r) {
         const double beta = 2.0 / 3.0 - (r == 0 ? 0.0 : cprev / 6.0);
@@ -571,6 +592,10 @@ vp_status vp_create(const vp_grid *grid, int32_t basis, const vp_pusher *pusher,
     const double beta_inf = 1.0 / 3.0 + 1.0 / (2.0 * sqrt(3.0));
     piv[2 * kPivots] = (1.0 / 6.0) / beta_inf;
     piv[2 * kPivots + 1] = 1.0 / beta_inf;
+    unit_gain_scale(piv[2 * kPivots + 1], piv[2 * kPivots], true, &piv[kPivXsFused],
+                    &piv[kPivXsFused + 1]);
+    unit_gain_scale(piv[2 * kPivots + 1], piv[2 * kPivots], false, &piv[kPivXsFilter],
+                    &piv[kPivXsFilter + 1]);
     // sigma = column sums of Lambda_p^{-1} (np x np tridiag(1/6, 2/3, 1/6), symmetric):
     // the Thomas solve of T sigma = 1
     std::vector<double> sigma(g.np, 1.0), cpv(g.np);

@@ -41,7 +41,7 @@ __device__ __forceinline__ int padx(int i) { return i + (i >> 5); }
 
 template <typename T>
 __global__ void filter_x_kernel(const T *__restrict__ in, T *__restrict__ out, int nx, int np,
-                                unsigned *err)
+                                const double *__restrict__ piv, unsigned *err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *buf = reinterpret_cast<T *>(smem_raw);
@@ -96,12 +96,15 @@ __global__ void filter_x_kernel(const T *__restrict__ in, T *__restrict__ out, i
         init *= cyc;
     }
     __syncthreads();
-    const T scale = (T)(-6.0 * kZ);
+    // FP64: the scale -6z; FP32: the unit-DC-gain scale of the step as a float pair
+    const bool f32 = sizeof(T) == 4;
+    const T sh = f32 ? (T)piv[kPivXsFilter] : (T)(-6.0 * kZ);
+    const T sl = f32 ? (T)piv[kPivXsFilter + 1] : T(0);
     if (active) {
         T u = init;
         for (int i = e - 1; i >= s; --i) {
             u = buf[padx(i)] + z * u;
-            buf[padx(i)] = u * scale;
+            buf[padx(i)] = f32 ? u * sh + u * sl : u * sh;
         }
     }
     __syncthreads();
@@ -192,13 +195,14 @@ __global__ void __launch_bounds__(kPCols *kPWarps)
 }  // namespace
 
 template <typename T>
-cudaError_t launch_filter_x(const T *in, T *out, int nx, int np, unsigned *err, cudaStream_t s)
+cudaError_t launch_filter_x(const T *in, T *out, int nx, int np, const double *piv, unsigned *err,
+                            cudaStream_t s)
 {
     const size_t smem = (size_t)(nx + nx / 32 + 1) * sizeof(T);
     cudaError_t e = cudaFuncSetAttribute(filter_x_kernel<T>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    filter_x_kernel<T><<<np, 256, smem, s>>>(in, out, nx, np, err);
+    filter_x_kernel<T><<<np, 256, smem, s>>>(in, out, nx, np, piv, err);
     return cudaGetLastError();
 }
 
@@ -224,10 +228,10 @@ cudaError_t launch_filter_p(const T *in, T *out, int nx, int np, const double *p
     return cudaGetLastError();
 }
 
-template cudaError_t launch_filter_x<float>(const float *, float *, int, int, unsigned *,
-                                            cudaStream_t);
-template cudaError_t launch_filter_x<double>(const double *, double *, int, int, unsigned *,
-                                             cudaStream_t);
+template cudaError_t launch_filter_x<float>(const float *, float *, int, int, const double *,
+                                            unsigned *, cudaStream_t);
+template cudaError_t launch_filter_x<double>(const double *, double *, int, int, const double *,
+                                             unsigned *, cudaStream_t);
 template cudaError_t launch_filter_p<float>(const float *, float *, int, int, const double *,
                                             const double2 *, double *, int, unsigned *,
                                             cudaStream_t);

@@ -78,7 +78,10 @@ struct FTaps<T, VP_BASIS_CUBIC_BSPLINE> {
         w[0] = s3 * sixth;
         w[3] = t3 * sixth;
         w[1] = two3 - t2 + T(0.5) * t3;
-        w[2] = two3 - s2 + T(0.5) * s3;
+        // the weights sum to one up to unbiased rounding: forming w[2] from the formula
+        // instead would carry the rounding of 2/3 (FP32: a mean excess of 4e-8 per axis)
+        // into the mass of every step
+        w[2] = (T(1) - (w[0] + w[3])) - w[1];
     }
 };
 
@@ -376,7 +379,7 @@ __device__ __forceinline__ int padc(int c) { return c + (c >> 3); }
 
 template <typename T, int kXMax>
 __device__ void solve_row_x(const T *row, int L, bool cyclic, int lane, T *v, int &per, int &base,
-                            bool padded)
+                            bool padded, T sh, T sl)
 {
     per = (L + 31) / 32;
     base = lane * per;
@@ -467,9 +470,9 @@ __device__ void solve_row_x(const T *row, int L, bool cyclic, int lane, T *v, in
         for (int k = 0; k < kXMax; ++k)
             if (k <= last) v[k] += zpow<T>(L - (base + k)) * unext;
     }
-    const T scale = T(-6) * z;
+    // the scale -6z; in FP32 the unit-DC-gain scale of the step as a float pair sh + sl
 #pragma unroll
-    for (int k = 0; k < kXMax; ++k) v[k] *= scale;
+    for (int k = 0; k < kXMax; ++k) v[k] = sizeof(T) == 4 ? v[k] * sh + v[k] * sl : v[k] * sh;
 }
 
 }  // namespace
@@ -479,7 +482,7 @@ template <typename T, int KX>
 __device__ __forceinline__ void gal_rows(T *win, const WinGeom &W, T *dst, int L, bool full, int D,
                                          int G, int Gp, int TXe, int TPe, int P0, int X0, int nx,
                                          bool want_part, int warp, int nwarps, int lane, bool &bad,
-                                         T *stage_all, int stage_len)
+                                         T *stage_all, int stage_len, T sh, T sl)
 {
     // per-warp padded copy of the row (conflict-free reads of contiguous chunks)
     const int plen = padc(L) + 8;
@@ -493,9 +496,9 @@ __device__ __forceinline__ void gal_rows(T *win, const WinGeom &W, T *dst, int L
         if (use_stage) {
             for (int c = lane; c < L; c += 32) stage[padc(c)] = row[c];
             __syncwarp();
-            solve_row_x<T, KX>(stage, L, full, lane, v, per, base, true);
+            solve_row_x<T, KX>(stage, L, full, lane, v, per, base, true, sh, sl);
         } else {
-            solve_row_x<T, KX>(row, L, full, lane, v, per, base, false);
+            solve_row_x<T, KX>(row, L, full, lane, v, per, base, false, sh, sl);
         }
         __syncwarp();
         // v - v is 0 for finite values and NaN otherwise
@@ -817,12 +820,15 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
     double pw = 0.0, pc = 0.0, ps = 0.0;
     if (GAL) {
         const int L = full ? nx : TXe + 2 * D;
+        const bool f32 = sizeof(T) == 4;
+        const T sh = f32 ? (T)A.piv[kPivXsFused] : T(-6) * T(-0.26794919243112270647);
+        const T sl = f32 ? (T)A.piv[kPivXsFused + 1] : T(0);
         if (L <= 256)
             gal_rows<T, 8>(win, W, A.dst, L, full, D, G, Gp, TXe, TPe, P0, X0, nx, want_part, warp,
-                           nwarps, lane, bad, gcol, GRows<T>::value * blockDim.x);
+                           nwarps, lane, bad, gcol, GRows<T>::value * blockDim.x, sh, sl);
         else
             gal_rows<T, kXBig>(win, W, A.dst, L, full, D, G, Gp, TXe, TPe, P0, X0, nx, want_part,
-                               warp, nwarps, lane, bad, gcol, GRows<T>::value * blockDim.x);
+                               warp, nwarps, lane, bad, gcol, GRows<T>::value * blockDim.x, sh, sl);
     } else {
         for (int k = tid; k < TXe * TPe; k += blockDim.x) {
             const int rr = k / TXe, c = k - rr * TXe;

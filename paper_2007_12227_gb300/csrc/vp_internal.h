@@ -150,12 +150,19 @@ template <typename T>
 cudaError_t launch_lambda_p_mul(const T *w, T *s, int nx, int np, cudaStream_t st);
 
 template <typename T>
-cudaError_t launch_filter_x(const T *in, T *out, int nx, int np, unsigned *err, cudaStream_t s);
+cudaError_t launch_filter_x(const T *in, T *out, int nx, int np, const double *piv, unsigned *err,
+                            cudaStream_t s);
 template <typename T>
 cudaError_t launch_filter_p(const T *in, T *out, int nx, int np, const double *piv,
                             const double2 *csx, double *part, int want_part, unsigned *err,
                             cudaStream_t s);
 constexpr int kPivots = 64;       // exact Thomas pivots kept for the first rows
+// Pivot table layout (doubles): [2 r] = c'_r, [2 r + 1] = 1 / beta_r for r < kPivots, then
+// their limits at [2 kPivots], [2 kPivots + 1]; then the FP32 Lambda_x scale of the one-pass
+// kernel and of the separate filters, each as a float pair hi + lo (see unit_gain_scale).
+constexpr int kPivXsFused = 2 * kPivots + 2;
+constexpr int kPivXsFilter = 2 * kPivots + 4;
+constexpr int kPivTable = 2 * kPivots + 6;
 int filter_p_blocks(int nx, int np);
 
 template <typename T>

@@ -58,7 +58,7 @@ struct Taps<T, VP_BASIS_CUBIC_BSPLINE> {
         w[0] = s * s * s * sixth;
         w[3] = t3 * sixth;
         w[1] = T(2) / T(3) - t2 + T(0.5) * t3;
-        w[2] = T(1) - w[0] - w[1] - w[3];
+        w[2] = (T(1) - (w[0] + w[3])) - w[1];   // partition of unity up to unbiased rounding
     }
 };
 
