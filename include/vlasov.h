@@ -186,6 +186,21 @@ vp_status vp_moments_static(const void *w, int32_t dtype, const vp_grid *grid,
                             const vp_pusher *pusher, double lost_mass, const double *a_re_im,
                             vp_moments_t *out, void *stream);
 
+/* What the planner chose for a simulation (read-only; no device work). */
+typedef struct vp_plan_info {
+    int32_t kernel;           /* VP_KERNEL_FUSED, VP_KERNEL_TILED or VP_KERNEL_SCATTER */
+    int32_t tile_x, tile_p;   /* destination tile (fused, tiled); whole mesh for scatter */
+    int32_t ntiles_x, ntiles_p;
+    int32_t threads;          /* threads per CTA of the fused step kernel, else 0 */
+    int32_t full_row;         /* fused: tiles span the whole x period */
+    int32_t state_is_s;       /* 1: the stored state is s = Lambda_p w (fused Galerkin) */
+    int32_t launches_per_step;/* kernels one vp_step(1) launches */
+    int32_t pad;
+    int64_t workspace_bytes;
+    int64_t smem_bytes;       /* dynamic shared memory per CTA of the step kernel */
+} vp_plan_info;
+vp_status vp_plan(const vp_sim *sim, vp_plan_info *out);
+
 /* Redirect later work to another stream (no synchronisation is implied). */
 vp_status vp_set_stream(vp_sim *sim, void *stream);
 
@@ -271,6 +286,61 @@ vp_status vp_server_take_f(vp_server *srv, uint64_t id, void *host, int32_t dtyp
 double vp_server_clock(void);
 void vp_server_destroy(vp_server *srv);
 const char *vp_server_last_error(const vp_server *srv);
+
+/* ---------------------------------------------------------------- autotuning
+ * Chooses the destination tile shape of the step kernel (vp_opts.tile_x,
+ * tile_p) by timing candidate shapes on the device: the planner's default and a
+ * fixed list of widths and heights (shapes the planner rejects, or plans onto
+ * another kernel, are dropped; shapes that plan to the same tiles are timed
+ * once). Every
+ * candidate is created in the caller's workspace, filled with a constant
+ * density, warmed up and timed with CUDA events on opts->stream over at least
+ * min_steps steps and min_ms of device time (the better of two runs). The
+ * tile shape has no effect on the arithmetic of a node: every candidate
+ * computes the same step. batched = 1 times the `count` configurations
+ * together, each candidate shape applied to all of them as one vp_batch
+ * (FP32, one-pass kernel); batched = 0 tunes count = 1 configuration alone.
+ * FEL configurations are timed at their A0; the windows grow with |A|.
+ * Results are kept in a process-wide cache keyed by the configurations (all
+ * grid and pusher fields except A0) and the options, so a second call with
+ * the same key times nothing (from_cache = 1). Synchronises opts->stream. */
+typedef struct vp_tune_config {
+    vp_grid grid;
+    int32_t basis;
+    int32_t pad;
+    vp_pusher pusher;
+} vp_tune_config;
+
+typedef struct vp_tune_opts {
+    int32_t min_steps;     /* timed steps per candidate, at least (0 = 3) */
+    int32_t batched;       /* 1: time the configurations together as one batch */
+    int32_t use_cache;     /* 1: read and fill the process-wide cache */
+    int32_t pad;
+    double min_ms;         /* device time per candidate, at least (0 = 2 ms) */
+} vp_tune_opts;
+
+typedef struct vp_tune_result {
+    int32_t tile_x, tile_p;      /* chosen shape, as vp_opts.tile_x and tile_p reproduce it */
+    int32_t kernel;              /* kernel of that plan (VP_KERNEL_*) */
+    int32_t candidates;          /* distinct shapes timed */
+    int32_t from_cache;
+    int32_t pad;
+    double ms_per_step;          /* one step with the chosen shape (batched: the whole batch) */
+    double default_ms_per_step;  /* the same with the planner's default shape */
+} vp_tune_result;
+
+/* Bytes of device workspace vp_autotune() needs (the largest candidate, all
+ * configurations at once when batched, plus a density buffer). */
+vp_status vp_autotune_workspace_size(const vp_tune_config *cfgs, int32_t count, const vp_opts *opts,
+                                     const vp_tune_opts *topts, size_t *bytes);
+/* cfgs: count configurations; opts: precision, projection, kernel, history
+ * capacity and stream shared by all (its tile fields are ignored); out: count
+ * results (batched: one shape for all, as each configuration plans it). */
+vp_status vp_autotune(const vp_tune_config *cfgs, int32_t count, const vp_opts *opts,
+                      const vp_tune_opts *topts, void *workspace, size_t workspace_bytes,
+                      vp_tune_result *out);
+/* Forget every cached tuning result. */
+void vp_autotune_clear_cache(void);
 
 #ifdef __cplusplus
 }

@@ -899,6 +899,35 @@ vp_status vp_state_device(vp_sim *s, void **dev)
     return st;
 }
 
+vp_status vp_plan(const vp_sim *s, vp_plan_info *out)
+{
+    if (!s || !out) return VP_ERR_ARG;
+    const Plan &P = s->P;
+    memset(out, 0, sizeof(*out));
+    out->kernel = P.kernel;
+    out->tile_x = P.kernel == VP_KERNEL_SCATTER ? P.g.nx : P.tx;
+    out->tile_p = P.kernel == VP_KERNEL_SCATTER ? P.g.np : P.tp;
+    out->ntiles_x = P.kernel == VP_KERNEL_SCATTER ? 1 : P.ntx;
+    out->ntiles_p = P.kernel == VP_KERNEL_SCATTER ? 1 : P.ntp;
+    out->threads = P.kernel == VP_KERNEL_FUSED ? P.threads : 0;
+    out->full_row = P.full_row ? 1 : 0;
+    out->state_is_s = P.state_s ? 1 : 0;
+    // step kernel (+ filters along x and p) (+ FEL partials) + field update or step counter
+    int n = 2;
+    if (P.kernel != VP_KERNEL_FUSED && P.galerkin) n += 2;
+    if (P.kernel == VP_KERNEL_SCATTER && P.fel && !P.galerkin) n += 1;
+    out->launches_per_step = n;
+    out->workspace_bytes = (int64_t)P.L.total;
+    const bool f64 = P.precision == VP_FP64;
+    if (P.kernel == VP_KERNEL_FUSED)
+        out->smem_bytes = (int64_t)(f64 ? fused_smem_bytes<double>(P.ws, P.tp + 2 * P.Gp, P.threads)
+                                        : fused_smem_bytes<float>(P.ws, P.tp + 2 * P.Gp, P.threads));
+    else if (P.kernel == VP_KERNEL_TILED)
+        out->smem_bytes = (int64_t)(f64 ? tiled_smem_bytes<double>(P.tx, P.tp)
+                                        : tiled_smem_bytes<float>(P.tx, P.tp));
+    return VP_OK;
+}
+
 void vp_destroy(vp_sim *s) { delete s; }
 
 const char *vp_last_error(const vp_sim *s) { return s ? s->msg : "NULL simulation"; }
@@ -929,6 +958,8 @@ struct BatchLayout {
     size_t args, parity, items, counter, fin, total;
 };
 
+void batch_layout_of(int count, int items, BatchLayout *L);
+
 vp_status batch_layout(vp_sim *const *sims, int count, BatchLayout *L, int *nitems, char *msg)
 {
     if (!sims || count < 1) return fail(msg, VP_ERR_ARG, "batch needs at least one simulation");
@@ -946,6 +977,13 @@ vp_status batch_layout(vp_sim *const *sims, int count, BatchLayout *L, int *nite
             return fail(msg, VP_ERR_ARG, "simulation %d differs in basis or projection", k);
         items += P.ntx * P.ntp;
     }
+    batch_layout_of(count, items, L);
+    *nitems = items;
+    return VP_OK;
+}
+
+void batch_layout_of(int count, int items, BatchLayout *L)
+{
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
@@ -958,8 +996,6 @@ vp_status batch_layout(vp_sim *const *sims, int count, BatchLayout *L, int *nite
     L->counter = take(sizeof(int) * 4);
     L->fin = take(sizeof(BatchFinal) * count);
     L->total = off;
-    *nitems = items;
-    return VP_OK;
 }
 
 #define VP_BCUDA(b, ...)                                                                   \
@@ -980,6 +1016,13 @@ vp_status batch_enqueue_step(vp_batch *b)
 }
 
 }  // namespace
+
+size_t vp::batch_workspace_bytes(int count, int items)
+{
+    BatchLayout L;
+    batch_layout_of(count, items, &L);
+    return L.total;
+}
 
 extern "C" {
 

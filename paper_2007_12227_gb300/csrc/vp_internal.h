@@ -143,6 +143,8 @@ struct BatchFinal {
     double dt;
 };
 cudaError_t launch_batch_finalize(const BatchFinal *fin, int ninst, int *parity, cudaStream_t s);
+// device bytes of a batch of `count` simulations with `items` tiles in all
+size_t batch_workspace_bytes(int count, int items);
 constexpr int fused_halo(int precision) { return precision == VP_FP64 ? 28 : 16; }
 constexpr int kFusedMaxRow = 512; // longest window row one warp solves
 constexpr int kFusedMaxTileP = 256; // tallest tile of the fused kernel

@@ -69,6 +69,33 @@ class vp_result(C.Structure):
                 ("moments", vp_moments_t)]
 
 
+class vp_plan_info(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in (
+        "kernel", "tile_x", "tile_p", "ntiles_x", "ntiles_p", "threads", "full_row", "state_is_s",
+        "launches_per_step", "pad")] + [("workspace_bytes", C.c_int64), ("smem_bytes", C.c_int64)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_ if n != "pad"}
+
+
+class vp_tune_config(C.Structure):
+    _fields_ = [("grid", vp_grid), ("basis", C.c_int32), ("pad", C.c_int32), ("pusher", vp_pusher)]
+
+
+class vp_tune_opts(C.Structure):
+    _fields_ = [("min_steps", C.c_int32), ("batched", C.c_int32), ("use_cache", C.c_int32),
+                ("pad", C.c_int32), ("min_ms", C.c_double)]
+
+
+class vp_tune_result(C.Structure):
+    _fields_ = [("tile_x", C.c_int32), ("tile_p", C.c_int32), ("kernel", C.c_int32),
+                ("candidates", C.c_int32), ("from_cache", C.c_int32), ("pad", C.c_int32),
+                ("ms_per_step", C.c_double), ("default_ms_per_step", C.c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_ if n != "pad"}
+
+
 _lib = None
 
 # (name, restype, argtypes) for every function of include/vlasov.h
@@ -108,6 +135,13 @@ _SIGNATURES = [
     ("vp_moments_static", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(vp_grid), C.POINTER(vp_pusher),
                                     C.c_double, C.POINTER(C.c_double), C.POINTER(vp_moments_t),
                                     C.c_void_p]),
+    ("vp_plan", C.c_int, [C.c_void_p, C.POINTER(vp_plan_info)]),
+    ("vp_autotune_workspace_size", C.c_int, [C.POINTER(vp_tune_config), C.c_int32, C.POINTER(vp_opts),
+                                             C.POINTER(vp_tune_opts), C.POINTER(C.c_size_t)]),
+    ("vp_autotune", C.c_int, [C.POINTER(vp_tune_config), C.c_int32, C.POINTER(vp_opts),
+                              C.POINTER(vp_tune_opts), C.c_void_p, C.c_size_t,
+                              C.POINTER(vp_tune_result)]),
+    ("vp_autotune_clear_cache", None, []),
     ("vp_destroy", None, [C.c_void_p]),
     ("vp_last_error", C.c_char_p, [C.c_void_p]),
     ("vp_status_string", C.c_char_p, [C.c_int]),
@@ -229,6 +263,15 @@ class Sim:
         dt = VP_FP64 if out.dtype == torch.float64 else VP_FP32
         _check(lib().vp_get_f_device(self.h, C.c_void_p(out.data_ptr()), dt, out.numel()), self.h)
         return out
+
+    def plan(self) -> dict:
+        """What the planner chose (kernel, tile shape, threads, launches per step, bytes)."""
+        pi = vp_plan_info()
+        _check(lib().vp_plan(self.h, C.byref(pi)), self.h)
+        return pi.as_dict()
+
+    def kernel(self) -> int:
+        return self.plan()["kernel"]
 
     def moments(self) -> dict:
         m = vp_moments_t()
@@ -376,3 +419,40 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def tune_configs(workloads):
+    """vp_tune_config array for objects with .grid, .basis and .pusher."""
+    arr = (vp_tune_config * len(workloads))()
+    for k, w in enumerate(workloads):
+        arr[k].grid = make_grid(w.grid)
+        arr[k].basis = int(w.basis)
+        arr[k].pusher = make_pusher(w.pusher)
+    return arr
+
+
+def autotune(workloads, precision=VP_FP32, projection=VP_PROJ_GALERKIN, kernel=VP_KERNEL_AUTO,
+             batched=False, min_steps=0, min_ms=0.0, use_cache=True, stream=None, device="cuda"):
+    """Tile shapes chosen by the library's autotuner (vp_autotune); one dict per workload.
+
+    The tuning workspace is a temporary torch allocation, released on return."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    cfgs = tune_configs(list(workloads))
+    n = len(cfgs)
+    opts = vp_opts(precision, projection, kernel, 0, 0, 0, C.c_void_p(stream.cuda_stream))
+    topts = vp_tune_opts(int(min_steps), 1 if batched else 0, 1 if use_cache else 0, 0, float(min_ms))
+    nbytes = C.c_size_t()
+    _check(lib().vp_autotune_workspace_size(cfgs, n, C.byref(opts), C.byref(topts), C.byref(nbytes)))
+    ws = torch.empty(nbytes.value + 256, dtype=torch.uint8, device=device)
+    aligned = (ws.data_ptr() + 255) // 256 * 256
+    out = (vp_tune_result * n)()
+    _check(lib().vp_autotune(cfgs, n, C.byref(opts), C.byref(topts), C.c_void_p(aligned),
+                             nbytes.value, out))
+    del ws
+    return [out[k].as_dict() for k in range(n)]
+
+
+def autotune_clear_cache():
+    lib().vp_autotune_clear_cache()

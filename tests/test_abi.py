@@ -48,16 +48,20 @@ def test_every_declared_function_is_exported_and_bound(lib):
 def test_struct_layouts_match_the_header(tmp_path):
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "vlasov.h"\n'
-                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(vp_grid), '
-                   'sizeof(vp_pusher), sizeof(vp_opts), sizeof(vp_moments_t), '
+                   'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", '
+                   'sizeof(vp_grid), sizeof(vp_pusher), sizeof(vp_opts), sizeof(vp_moments_t), '
                    'offsetof(vp_moments_t, step), sizeof(vp_server_opts), sizeof(vp_request), '
-                   'sizeof(vp_result), offsetof(vp_request, f0)); return 0;}\n')
+                   'sizeof(vp_result), offsetof(vp_request, f0), sizeof(vp_plan_info), '
+                   'sizeof(vp_tune_config), sizeof(vp_tune_opts), sizeof(vp_tune_result), '
+                   'offsetof(vp_tune_config, pusher)); return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
     got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     want = [C.sizeof(V.vp_grid), C.sizeof(V.vp_pusher), C.sizeof(V.vp_opts),
             C.sizeof(V.vp_moments_t), V.vp_moments_t.step.offset, C.sizeof(V.vp_server_opts),
-            C.sizeof(V.vp_request), C.sizeof(V.vp_result), V.vp_request.f0.offset]
+            C.sizeof(V.vp_request), C.sizeof(V.vp_result), V.vp_request.f0.offset,
+            C.sizeof(V.vp_plan_info), C.sizeof(V.vp_tune_config), C.sizeof(V.vp_tune_opts),
+            C.sizeof(V.vp_tune_result), V.vp_tune_config.pusher.offset]
     assert got == want
 
 
@@ -161,3 +165,32 @@ def test_server_host_paths_without_a_gpu(lib):
     bad = V.vp_request(12, V.vp_grid(8, 8, 0, 1, 0, 1), 1, V.vp_pusher(), 0, 0, -1, 0, None, 0)
     assert lib.vp_server_submit(h, C.byref(bad)) == V.VP_ERR_ARG
     lib.vp_server_destroy(h)
+
+
+def _tune_cfg(nx, np_):
+    g, b, pu, o = _cfg(nx=nx, np_=np_)
+    c = V.vp_tune_config()
+    c.grid, c.basis, c.pusher = g, b, pu
+    return c, o
+
+
+def test_autotune_host_checks(lib):
+    c, o = _tune_cfg(1024, 512)
+    cfgs = (V.vp_tune_config * 2)(c, c)
+    t = V.vp_tune_opts(0, 0, 0, 0, 0.0)
+    n = C.c_size_t()
+    assert lib.vp_autotune_workspace_size(cfgs, 1, C.byref(o), C.byref(t), C.byref(n)) == V.VP_OK
+    # the tuning workspace holds the largest candidate plan and a density buffer
+    assert n.value >= V.vp_workspace_size(c.grid, c.basis, c.pusher, o) + 4 * 1024 * 512
+    # several configurations are tuned only together (batched)
+    assert lib.vp_autotune_workspace_size(cfgs, 2, C.byref(o), C.byref(t), C.byref(n)) == V.VP_ERR_ARG
+    tb = V.vp_tune_opts(0, 1, 0, 0, 0.0)
+    assert lib.vp_autotune_workspace_size(cfgs, 2, C.byref(o), C.byref(tb), C.byref(n)) == V.VP_OK
+    o64 = V.vp_opts(V.VP_FP64, 0, 0, 0, 0, 0, None)
+    assert lib.vp_autotune_workspace_size(cfgs, 2, C.byref(o64), C.byref(tb),
+                                          C.byref(n)) == V.VP_ERR_UNSUPPORTED
+    out = (V.vp_tune_result * 1)()
+    # no workspace: refused before any device work
+    assert lib.vp_autotune(cfgs, 1, C.byref(o), C.byref(t), None, 0, out) == V.VP_ERR_WORKSPACE
+    assert lib.vp_autotune(cfgs, 0, C.byref(o), C.byref(t), None, 0, out) == V.VP_ERR_ARG
+    lib.vp_autotune_clear_cache()
