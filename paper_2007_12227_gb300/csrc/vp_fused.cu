@@ -475,6 +475,63 @@ __device__ void solve_row_x(const T *row, int L, bool cyclic, int lane, T *v, in
     for (int k = 0; k < kXMax; ++k) v[k] = sizeof(T) == 4 ? v[k] * sh + v[k] * sl : v[k] * sh;
 }
 
+// z^n for the pole z = sqrt(3) - 2, at compile time
+constexpr double zconst(int n)
+{
+    double r = 1.0;
+    for (int k = 0; k < n; ++k) r *= -0.26794919243112270647;
+    return r;
+}
+
+// Lambda_x^{-1} of one window row of exactly 32 KX elements (the common case of the
+// windowed tiles): the recurrences start from zero at both row ends and every power of z
+// the lane sweeps and the warp scans need is a compile-time constant.
+template <typename T, int KX>
+__device__ __forceinline__ void solve_row_x_exact(const T *row, int lane, T *v, bool padded, T sh,
+                                                  T sl)
+{
+    const int base = lane * KX;
+    const T z = (T)zconst(1);
+#pragma unroll
+    for (int k = 0; k < KX; ++k) v[k] = row[padded ? padc(base + k) : base + k];
+    // causal y_i = x_i + z y_{i-1}: lane-local, then the carry of the lanes below
+    T y = T(0);
+#pragma unroll
+    for (int k = 0; k < KX; ++k) {
+        y = v[k] + z * y;
+        v[k] = y;
+    }
+    T endv = y;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const T o = __shfl_up_sync(0xffffffffu, endv, 1 << s);
+        if (lane >= (1 << s)) endv += (T)zconst(KX << s) * o;
+    }
+    T carry = __shfl_up_sync(0xffffffffu, endv, 1);
+    if (lane == 0) carry = T(0);
+#pragma unroll
+    for (int k = 0; k < KX; ++k) v[k] += (T)zconst(k + 1) * carry;
+    // anticausal u_i = y_i + z u_{i+1}
+    T u = T(0);
+#pragma unroll
+    for (int k = KX - 1; k >= 0; --k) {
+        u = v[k] + z * u;
+        v[k] = u;
+    }
+    T startv = u;
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const T o = __shfl_down_sync(0xffffffffu, startv, 1 << s);
+        if (lane + (1 << s) < 32) startv += (T)zconst(KX << s) * o;
+    }
+    T carry2 = __shfl_down_sync(0xffffffffu, startv, 1);
+    if (lane == 31) carry2 = T(0);
+#pragma unroll
+    for (int k = 0; k < KX; ++k) v[k] += (T)zconst(KX - k) * carry2;
+#pragma unroll
+    for (int k = 0; k < KX; ++k) v[k] = sizeof(T) == 4 ? v[k] * sh + v[k] * sl : v[k] * sh;
+}
+
 }  // namespace
 
 // Lambda_x solve of the tile's window rows (one warp per row) and the tile store.
@@ -493,15 +550,20 @@ __device__ __forceinline__ void gal_rows(T *win, const WinGeom &W, T *dst, int L
         T *dst_row = dst + (size_t)(P0 + rr) * nx + X0 - D;
         T v[KX];
         int per, base;
+        const bool exact = !full && L == 32 * KX;
         if (use_stage) {
             for (int c = lane; c < L; c += 32) stage[padc(c)] = row[c];
             __syncwarp();
-            solve_row_x<T, KX>(stage, L, full, lane, v, per, base, true, sh, sl);
+        }
+        if (exact) {
+            solve_row_x_exact<T, KX>(use_stage ? stage : row, lane, v, use_stage, sh, sl);
+            per = KX;
+            base = lane * KX;
         } else {
-            solve_row_x<T, KX>(row, L, full, lane, v, per, base, false, sh, sl);
+            solve_row_x<T, KX>(use_stage ? stage : row, L, full, lane, v, per, base, use_stage, sh, sl);
         }
         __syncwarp();
-        // v - v is 0 for finite values and NaN otherwise
+        // v * 0 is 0 for finite values and NaN otherwise
         T chk = T(0);
         T *dp = dst_row + base;
         const bool inside = per == KX && base >= D && base + KX <= D + TXe;
@@ -516,7 +578,7 @@ __device__ __forceinline__ void gal_rows(T *win, const WinGeom &W, T *dst, int L
                 *reinterpret_cast<float4 *>(dp + k) = q;
             }
 #pragma unroll
-            for (int k = 0; k < KX; ++k) chk += v[k] - v[k];
+            for (int k = 0; k < KX; ++k) chk = fma(v[k], T(0), chk);
             if (want_part)
 #pragma unroll
                 for (int k = 0; k < KX; ++k) row[base + k] = v[k];   // keep s for the column sums
@@ -526,7 +588,7 @@ __device__ __forceinline__ void gal_rows(T *win, const WinGeom &W, T *dst, int L
                 const int c = base + k;
                 if (k < per && c >= D && c < D + TXe) {
                     dst_row[c] = v[k];
-                    chk += v[k] - v[k];
+                    chk = fma(v[k], T(0), chk);
                     if (want_part) row[c] = v[k];   // keep s for the column sums
                 }
             }
@@ -856,7 +918,8 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
     }
     if (bad) atomicOr(A.err, ERRF_NONFINITE);
 
-    // ---- per-tile reductions in a fixed order
+    // ---- per-tile reductions in a fixed order (FP64 work only where there is weight to sum)
+    if (!__syncthreads_or(lost != 0.0 || want_part)) return;
     double vals[4] = {lost, pw, pc, ps};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
