@@ -373,10 +373,91 @@ struct ColC {
     T uf, vf, cu1, cu2, cv1, cv2;
 };
 
+// FP32 pairs (x half, p half) in one 64-bit register, for packed FADD2 / FMUL2 / FFMA2
+typedef unsigned long long f2_t;
+__device__ __forceinline__ f2_t f2_pack(float a, float b)
+{
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2_t r, float &a, float &b)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ f2_t f2_add(f2_t a, f2_t b)
+{
+    f2_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b)
+{
+    f2_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c)
+{
+    f2_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+// FP32 node: push and tap weights of the x and p axes together in packed pairs. The base
+// cell is round(x - 1/2), so the fraction t lies in [0, 1] (t = 1 at an exact node gives
+// the same deposit as t = 0 one cell further: the B3 and tent kernels are continuous).
+template <int BASIS, bool UTERM>
+__device__ __forceinline__ void node_taps_f32(const ColC<float> &c, const RowEntry<float> &r,
+                                              int colrel, int rowrel, float w, int &m, int &n,
+                                              float *wx, float *wy)
+{
+    const float4 q0 = __ldg(reinterpret_cast<const float4 *>(&r));       // ui, vi, uf, vf
+    const float4 q1 = __ldg(reinterpret_cast<const float4 *>(&r) + 1);   // cy, cy, sy, sy
+    f2_t F = f2_add(f2_pack(c.uf, c.vf), f2_pack(q0.z, q0.w));
+    F = f2_fma(f2_pack(UTERM ? c.cu1 : 0.f, c.cv1), f2_pack(q1.x, q1.y), F);
+    F = f2_fma(f2_pack(UTERM ? c.cu2 : 0.f, c.cv2), f2_pack(q1.z, q1.w), F);
+    const f2_t M1 = f2_pack(-1.f, -1.f), ONE = f2_pack(1.f, 1.f);
+    const f2_t MAG = f2_pack(12582912.f, 12582912.f);   // 1.5 * 2^23
+    const f2_t TT = f2_add(f2_add(F, f2_pack(-0.5f, -0.5f)), MAG);
+    const f2_t R = f2_add(TT, f2_pack(-12582912.f, -12582912.f));
+    const f2_t T = f2_fma(R, M1, F);
+    float tu_bits, tv_bits;
+    f2_unpack(TT, tu_bits, tv_bits);
+    const int iu = __float_as_int(tu_bits) - 0x4B400000, iv = __float_as_int(tv_bits) - 0x4B400000;
+    using TP = FTaps<float, BASIS>;
+    m = colrel + c.ui + __float_as_int(q0.x) + iu + TP::LO;
+    n = rowrel + c.vi + __float_as_int(q0.y) + iv + TP::LO;
+    const f2_t S = f2_fma(T, M1, ONE);
+    if (BASIS == VP_BASIS_TENT) {
+        f2_unpack(S, wx[0], wy[0]);
+        f2_unpack(T, wx[1], wy[1]);
+    } else {
+        const f2_t T2 = f2_mul(T, T), S2 = f2_mul(S, S);
+        const f2_t T3 = f2_mul(T2, T), S3 = f2_mul(S2, S);
+        const float sixth = 1.f / 6.f, two3 = 2.f / 3.f;
+        const f2_t SIX = f2_pack(sixth, sixth);
+        const f2_t W0 = f2_mul(S3, SIX), W3 = f2_mul(T3, SIX);
+        const f2_t W1 = f2_fma(T3, f2_pack(0.5f, 0.5f), f2_fma(T2, M1, f2_pack(two3, two3)));
+        // the weights sum to one up to unbiased rounding (as in the scalar form)
+        const f2_t W2 = f2_fma(W1, M1, f2_fma(f2_add(W0, W3), M1, ONE));
+        f2_unpack(W0, wx[0], wy[0]);
+        f2_unpack(W1, wx[1], wy[1]);
+        f2_unpack(W2, wx[2], wy[2]);
+        f2_unpack(W3, wx[3], wy[3]);
+    }
+#pragma unroll
+    for (int b = 0; b < TP::N; ++b) wy[b] *= w;
+}
+
 template <typename T, int BASIS, bool UTERM>
 __device__ __forceinline__ void node_taps(const ColC<T> &c, const RowEntry<T> &r, int colrel,
                                           int rowrel, T w, int &m, int &n, T *wx, T *wy)
 {
+    if constexpr (sizeof(T) == 4) {
+        node_taps_f32<BASIS, UTERM>(c, r, colrel, rowrel, w, m, n, wx, wy);
+        return;
+    }
     using TP = FTaps<T, BASIS>;
     T fu = c.uf + r.uf;
     if (UTERM) fu += c.cu1 * r.cy + c.cu2 * r.sy;

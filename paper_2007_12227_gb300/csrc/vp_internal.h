@@ -29,9 +29,10 @@ struct ColEntry {
 };
 
 template <typename T>
-struct __align__(16) RowEntry {   // padded so that a row loads with two vector loads
+struct __align__(16) RowEntry {   // FP32: 32 bytes, two vector loads
     int ui, vi;
-    T uf, vf, sy, cy;
+    T uf, vf;
+    T cy, cy2, sy, sy2;   // cy2 = cy, sy2 = sy: (cos, cos) and (sin, sin) pairs for packed math
 };
 
 // FP64 per-row values used only to bound the source window of a tile.

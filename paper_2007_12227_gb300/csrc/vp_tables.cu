@@ -100,6 +100,8 @@ __global__ void row_kernel(Geometry g, RowEntry<T> *row, RowBound *rowb)
     e.vf = (T)f;
     e.sy = (T)sin(y);
     e.cy = (T)cos(y);
+    e.sy2 = e.sy;
+    e.cy2 = e.cy;
     row[j] = e;
     RowBound b;
     b.u = U;
