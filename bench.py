@@ -62,6 +62,21 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of x over all ranks (the replicas' slowest time), x on every rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world_size, units_per_rank, seconds_max):
+    """Units processed by all replicas divided by the slowest replica's time."""
+    return world_size * units_per_rank / seconds_max
+
+
 def workload(size):
     return I.pendulum_8192_fp32_cubic(size, size)
 
@@ -336,12 +351,9 @@ def main():
     clocks = sampler.stop() if sampler else None
     ms = ev0.elapsed_time(ev1)
     sim.sync()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, "cuda")
     ms_per_step = ms / args.steps
-    value = ws * N * args.steps / (ms * 1e-3)
+    value = whole_job_rate(ws, N * args.steps, ms * 1e-3)
     # kernels per vp_step on this plan: the one-pass step kernel and the step counter
     # (FEL: the field update); the separate-filter plan adds the two Lambda solves
     launches_per_step = 2 if sim.kernel() == V.VP_KERNEL_FUSED else 4
@@ -388,12 +400,8 @@ def main():
             sim.set_f_host_ptr(host_in.data_ptr(), V.VP_FP32)
             sim.step(1)
             sim.get_f_host_ptr(host_out.data_ptr(), V.VP_FP32)
-        wall = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([wall], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            wall = float(t.item())
-        e2e = {"value": ws * N * ke / wall, "unit": UNIT, "h2d_bytes_per_step": 4 * N,
+        wall = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+        e2e = {"value": whole_job_rate(ws, N * ke, wall), "unit": UNIT, "h2d_bytes_per_step": 4 * N,
                "d2h_bytes_per_step": 4 * N, "steps": ke,
                "note": "per step: vp_set_f from pinned host + vp_step(1) + vp_get_f to pinned host"}
 
