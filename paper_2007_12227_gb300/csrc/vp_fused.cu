@@ -957,12 +957,22 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
                     T gv = T(0);
                     if (c_lo - kHalo > kPivots) {
                         // far from the first row the pivots have their limits
-#pragma unroll 4
-                        for (; rr < c_lo; ++rr, sp += nx) gv = *sp * ib_inf - ib6_inf * gv;
-#pragma unroll 4
-                        for (; rr <= c_hi; ++rr, sp += nx) {
-                            gv = *sp * ib_inf - ib6_inf * gv;
-                            gc[(rr - c_lo) * nth] = gv;
+                        if (c_hi - c_lo + 1 == kC) {
+                            // whole chunk: warm-up and chunk rows as one unrolled sweep, so that all
+                            // of its loads are in flight before the recurrence needs them
+#pragma unroll
+                            for (int k = 0; k < kHalo + kC; ++k) {
+                                gv = __ldg(sp + (size_t)k * nx) * ib_inf - ib6_inf * gv;
+                                if (k >= kHalo) gc[(k - kHalo) * nth] = gv;
+                            }
+                        } else {
+#pragma unroll 16
+                            for (; rr < c_lo; ++rr, sp += nx) gv = *sp * ib_inf - ib6_inf * gv;
+#pragma unroll 16
+                            for (; rr <= c_hi; ++rr, sp += nx) {
+                                gv = *sp * ib_inf - ib6_inf * gv;
+                                gc[(rr - c_lo) * nth] = gv;
+                            }
                         }
                     } else {
                         for (; rr < c_lo; ++rr, sp += nx) gv = (*sp - sixth * gv) * piv_ib[min(rr, kPivots)];
