@@ -204,7 +204,8 @@ vp_status vp_plan(const vp_sim *sim, vp_plan_info *out);
 /* Redirect later work to another stream (no synchronisation is implied). */
 vp_status vp_set_stream(vp_sim *sim, void *stream);
 
-/* Device pointer of the current weights (valid until the next vp_step). */
+/* Device pointer of the current weights (valid until the next vp_step), for reading:
+ * change the state only through vp_set_f / vp_set_f_device. */
 vp_status vp_state_device(vp_sim *sim, void **dev);
 
 void vp_destroy(vp_sim *sim);

@@ -28,7 +28,7 @@ constexpr int kMoutLen = 32;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t f0, f1, tmp, col, row, rowb, vcb, rowbf, vcbf, csx, ucol, vcol, piv, sigma, state, hist,
+    size_t f0, f1, tmp, col, row, rowb, vcb, rowbf, vcbf, csx, ucol, vcol, piv, sigma, smax, state, hist,
         lost, part, mpart, mout, err, total;
 };
 
@@ -238,6 +238,8 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     L.vcol = take(grid->nx * sizeof(double));
     L.piv = take(kPivTable * sizeof(double));
     L.sigma = take(grid->np * sizeof(double));
+    // FP32 one-pass plans: max|s| per tile of each state buffer (the fixed-point window scale)
+    L.smax = take(kernel == VP_KERNEL_FUSED && sz == 4 ? 2 * (size_t)P->ntx * P->ntp * sizeof(float) : 0);
     L.state = take(ST_NSTATE * sizeof(double));
     L.hist = take((size_t)P->hist_cap * 2 * sizeof(double));
     L.lost = take(P->nlost * sizeof(double));
@@ -343,6 +345,12 @@ FusedArgs<T> fused_args(vp_sim *s, const void *src, void *dst)
     a.state = s->ptr<double>(P.L.state);
     a.piv = s->ptr<double>(P.L.piv);
     a.sigma = s->ptr<double>(P.L.sigma);
+    {
+        float *m0 = s->ptr<float>(P.L.smax), *m1 = m0 + (size_t)P.ntx * P.ntp;
+        const bool from0 = src == s->f(0);
+        a.smax_in = from0 ? m0 : m1;
+        a.smax_out = from0 ? m1 : m0;
+    }
     a.csx = s->ptr<double2>(P.L.csx);
     a.tile_lost = s->ptr<double>(P.L.lost);
     a.tile_part = s->ptr<double>(P.L.part);
@@ -688,6 +696,10 @@ static vp_status set_f_common(vp_sim *s, const void *src, int32_t dtype, size_t 
                                                   static_cast<float *>(s->f(0)), P.g.nx, P.g.np,
                                                   s->stream));
     }
+    if (P.kernel == VP_KERNEL_FUSED && P.precision == VP_FP32)
+        VP_CUDA(s, launch_tile_max(static_cast<const float *>(s->f(0)), s->ptr<float>(P.L.smax), P.g.nx,
+                                   P.g.np, P.tx, P.tp, P.ntx, P.ntp, s->ptr<unsigned>(P.L.err),
+                                   s->stream));
     return VP_OK;
 }
 

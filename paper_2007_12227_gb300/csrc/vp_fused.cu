@@ -644,7 +644,7 @@ template <typename T, int KX>
 __device__ __forceinline__ void gal_rows(T *win, const WinGeom &W, T *dst, int L, bool full, int D,
                                          int G, int Gp, int TXe, int TPe, int P0, int X0, int nx,
                                          bool want_part, int warp, int nwarps, int lane, bool &bad,
-                                         T *stage_all, int stage_len, T sh, T sl, T iq)
+                                         T *stage_all, int stage_len, T sh, T sl, T iq, float &om)
 {
     // per-warp padded copy of the row (conflict-free reads of contiguous chunks)
     const int plen = padc(L) + 8;
@@ -687,6 +687,9 @@ __device__ __forceinline__ void gal_rows(T *win, const WinGeom &W, T *dst, int L
             }
 #pragma unroll
             for (int k = 0; k < KX; ++k) chk = fma(v[k], T(0), chk);
+            if (sizeof(T) == 4)
+#pragma unroll
+                for (int k = 0; k < KX; ++k) om = fmaxf(om, fabsf((float)v[k]));
             if (want_part)
 #pragma unroll
                 for (int k = 0; k < KX; ++k) row[base + k] = v[k];   // keep s for the column sums
@@ -697,6 +700,7 @@ __device__ __forceinline__ void gal_rows(T *win, const WinGeom &W, T *dst, int L
                 if (k < per && c >= D && c < D + TXe) {
                     dst_row[c] = v[k];
                     chk = fma(v[k], T(0), chk);
+                    om = fmaxf(om, fabsf((float)v[k]));
                     if (want_part) row[c] = v[k];   // keep s for the column sums
                 }
             }
@@ -716,7 +720,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
     constexpr int R = (BASIS == VP_BASIS_TENT) ? 1 : 2;
     T *win = reinterpret_cast<T *>(smem_raw);
     T *gcol = win + (size_t)A.ws * (A.tp + 2 * A.Gp);   // [GRows][blockDim] column buffer (Galerkin)
-    __shared__ int s_ia, s_ib, s_ja, s_jb, s_smax;
+    __shared__ int s_ia, s_ib, s_ja, s_jb, s_smax, s_omax;
     __shared__ double s_r4[4][kFusedMaxThreads / 32];
     // Thomas pivots of tridiag(1/6, 2/3, 1/6) in T: entry kPivots holds the limit
     __shared__ T piv_cp[kPivots + 1], piv_ib[kPivots + 1];
@@ -763,6 +767,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
         s_ja = 0x7fffffff;
         s_jb = -0x7fffffff;
         s_smax = 0;
+        s_omax = 0;
     }
     double al = g.alpha0, be = g.beta0, M = g.m0, phi = g.phi0;
     if (g.kind == VP_PUSH_FEL_DKD) {
@@ -853,34 +858,31 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
     const int ia = s_ia, ib = s_ib, ja = s_ja, jb = s_jb;
     double lost = 0.0;   // in the window's scaled units until the end of the tile
 
-    // ---- FP32: fixed-point scale of the window from max|s| over the rows the walk reads.
+    // ---- FP32: fixed-point scale of the window from max|s| over the rows the walk reads, taken
+    //      from the per-tile maxima the previous step (or vp_set_f) recorded for the state.
     //      The truncated Thomas solve keeps |w| <= 3 max|s| (forward gain 1/(beta - 1/6) <= 2.2,
     //      back substitution 1/(1 - c') <= 1.37); a cell sums the B3 taps of the nodes pushed near
     //      it, about one for an area-preserving flow: 8 times that bound fits in int32.
     T qs = T(1), iq = T(1);
     if (sizeof(T) == 4) {
-        float mx = 0.f, chk = 0.f;
+        float mx = 0.f;
         if (jb >= ja) {
             const int r0 = GAL ? max(0, ja - kHalo) : ja, r1 = GAL ? min(np - 1, jb + kHalo) : jb;
             const int wsrc = min(ib - ia + 1, nx);
             for (int cidx = tid; cidx < wsrc; cidx += blockDim.x) {
-                const T *sp = A.src + imod(ia + cidx, nx) + (size_t)r0 * nx;
-                for (int r = r0; r <= r1; ++r, sp += nx) {
-                    const float v = (float)*sp;
-                    mx = fmaxf(mx, fabsf(v));
-                    chk = fmaf(v, 0.f, chk);   // NaN for a non-finite value
-                }
+                const int tc = imod(ia + cidx, nx) / A.tx;
+                for (int tr = r0 / A.tp; tr <= r1 / A.tp; ++tr) mx = fmaxf(mx, A.smax_in[tr * A.ntx + tc]);
             }
         }
-        if (mx > 0.f) atomicMax(&s_smax, __float_as_int(mx));
-        if (__syncthreads_or(chk != 0.f)) {
-            if (tid == 0) atomicOr(A.err, ERRF_NONFINITE);
-            qs = T(0);   // the deposit of a non-finite state is dropped; the step reports it
+        if (mx > 0.f && mx <= 3.0e38f) atomicMax(&s_smax, __float_as_int(mx));
+        if (__syncthreads_or(!(mx <= 3.0e38f))) {
+            qs = T(0);   // a non-finite state, reported when it was written: its deposit is dropped
+            iq = T(0);
         } else {
             const float m = fmaxf(__int_as_float(s_smax), 1e-30f) * (GAL ? 3.1f : 1.f) * 8.f;
             qs = (T)(2147483648.0f / m);
+            iq = T(1) / qs;
         }
-        iq = qs > T(0) ? T(1) / qs : T(0);
     }
 
     // ---- walk the source columns
@@ -983,7 +985,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
                     }
                     const RowEntry<T> *rp = A.row + c_hi;
                     if (c_lo > kPivots) {
-#pragma unroll 2
+#pragma unroll 1
                         for (int r = c_hi; r >= c_lo; --r, --rp) {
                             uv = gc[(r - c_lo) * nth] - cp_inf * uv;
                             int m, n;
@@ -1028,6 +1030,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
     // ---- store the tile (Galerkin: after the Lambda_x solve); FEL column sums
     const bool want_part = A.fel_partials != 0;
     bool bad = false;
+    float om = 0.f;   // FP32: max|s'| of the stored outputs
     double pw = 0.0, pc = 0.0, ps = 0.0;
     if (GAL) {
         const int L = full ? nx : TXe + 2 * D;
@@ -1036,15 +1039,17 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
         const T sl = f32 ? (T)A.piv[kPivXsFused + 1] : T(0);
         if (L <= 256)
             gal_rows<T, 8>(win, W, A.dst, L, full, D, G, Gp, TXe, TPe, P0, X0, nx, want_part, warp,
-                           nwarps, lane, bad, gcol, GRows<T>::value * blockDim.x, sh, sl, iq);
+                           nwarps, lane, bad, gcol, GRows<T>::value * blockDim.x, sh, sl, iq, om);
         else
             gal_rows<T, kXBig>(win, W, A.dst, L, full, D, G, Gp, TXe, TPe, P0, X0, nx, want_part,
-                               warp, nwarps, lane, bad, gcol, GRows<T>::value * blockDim.x, sh, sl, iq);
+                               warp, nwarps, lane, bad, gcol, GRows<T>::value * blockDim.x, sh, sl, iq,
+                               om);
     } else {
         for (int k = tid; k < TXe * TPe; k += blockDim.x) {
             const int rr = k / TXe, c = k - rr * TXe;
             const T v = wget(win + (size_t)(rr + Gp) * W.ws + G + c, iq);
             A.dst[(size_t)(P0 + rr) * nx + X0 + c] = v;
+            om = fmaxf(om, fabsf((float)v));
             bad |= !isfinite(v);
         }
     }
@@ -1069,7 +1074,11 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
     if (bad) atomicOr(A.err, ERRF_NONFINITE);
 
     // ---- per-tile reductions in a fixed order (FP64 work only where there is weight to sum)
-    if (!__syncthreads_or(lost != 0.0 || want_part)) return;
+    // FP32: record max|s'| of the tile for the next step's window scale
+    if (sizeof(T) == 4 && om > 0.f) atomicMax(&s_omax, __float_as_int(om));
+    const bool reduce = __syncthreads_or(lost != 0.0 || want_part);
+    if (sizeof(T) == 4 && tid == 0) A.smax_out[tile] = __int_as_float(s_omax);
+    if (!reduce) return;
     double vals[4] = {qs > T(0) ? lost / (double)qs : 0.0, pw, pc, ps};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -1175,6 +1184,41 @@ __global__ void lambda_p_mul_kernel(const T *__restrict__ w, T *__restrict__ s, 
         const T hi = j + 1 < np ? w[idx + nx] : T(0);
         s[idx] = (lo + hi) * (T(1) / T(6)) + c * (T(2) / T(3));
     }
+}
+
+// max|s| per tile (one CTA per tile); a non-finite value sets the error flag
+__global__ void tile_max_kernel(const float *__restrict__ s, float *__restrict__ map, int nx, int np,
+                                int tx, int tp, int ntx, unsigned *err)
+{
+    __shared__ int s_m, s_bad;
+    if (threadIdx.x == 0) {
+        s_m = 0;
+        s_bad = 0;
+    }
+    __syncthreads();
+    const int X0 = (blockIdx.x % ntx) * tx, P0 = (blockIdx.x / ntx) * tp;
+    const int TX = min(tx, nx - X0), TP = min(tp, np - P0);
+    float m = 0.f, chk = 0.f;
+    for (int k = threadIdx.x; k < TX * TP; k += blockDim.x) {
+        const int r = k / TX, c = k - r * TX;
+        const float v = s[(size_t)(P0 + r) * nx + X0 + c];
+        m = fmaxf(m, fabsf(v));
+        chk = fmaf(v, 0.f, chk);
+    }
+    if (m > 0.f) atomicMax(&s_m, __float_as_int(m));
+    if (chk != 0.f) s_bad = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        map[blockIdx.x] = s_bad ? __int_as_float(0x7f800000) : __int_as_float(s_m);
+        if (s_bad) atomicOr(err, ERRF_NONFINITE);
+    }
+}
+
+cudaError_t launch_tile_max(const float *s, float *map, int nx, int np, int tx, int tp, int ntx,
+                            int ntp, unsigned *err, cudaStream_t st)
+{
+    tile_max_kernel<<<ntx * ntp, 256, 0, st>>>(s, map, nx, np, tx, tp, ntx, err);
+    return cudaGetLastError();
 }
 
 template <typename T>

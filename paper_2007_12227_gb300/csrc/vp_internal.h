@@ -113,6 +113,10 @@ struct FusedArgs {
     int ws;                 // window row stride (elements)
     int full_row;           // tiles span the whole x period (ntx == 1)
     int fel_partials;
+    // FP32: max|state| per destination tile of the state read (in) and of the state written (out),
+    // [ntp][ntx]; it bounds the fixed-point window of the next step
+    const float *smax_in;
+    float *smax_out;
 };
 
 // ---- launch entry points (defined in the .cu files) -----------------------
@@ -151,6 +155,9 @@ constexpr int kFusedMaxRow = 512; // longest window row one warp solves
 constexpr int kFusedMaxTileP = 256; // tallest tile of the fused kernel
 template <typename T>
 cudaError_t launch_lambda_p_mul(const T *w, T *s, int nx, int np, cudaStream_t st);
+// max|s| of an FP32 state over each tile x tile_p tile into map[ntp][ntx]; non-finite -> err
+cudaError_t launch_tile_max(const float *s, float *map, int nx, int np, int tx, int tp, int ntx,
+                            int ntp, unsigned *err, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_filter_x(const T *in, T *out, int nx, int np, const double *piv, unsigned *err,
