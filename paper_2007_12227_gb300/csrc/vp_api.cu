@@ -28,7 +28,8 @@ constexpr int kMoutLen = 32;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t f0, f1, tmp, col, row, rowb, vcb, rowbf, vcbf, csx, ucol, vcol, piv, sigma, smax, state, hist,
+    size_t f0, f1, tmp, col, row, rowb, vcb, rowbf, vcbf, csx, ucol, vcol, piv, sigma, smax, tsrc, state,
+        hist,
         lost, part, mpart, mout, err, total;
 };
 
@@ -240,6 +241,8 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     L.sigma = take(grid->np * sizeof(double));
     // FP32 one-pass plans: max|s| per tile of each state buffer (the fixed-point window scale)
     L.smax = take(kernel == VP_KERNEL_FUSED && sz == 4 ? 2 * (size_t)P->ntx * P->ntp * sizeof(float) : 0);
+    // one-pass plans of a push fixed for the whole run: each tile's source rectangle
+    L.tsrc = take(kernel == VP_KERNEL_FUSED && !P->fel ? (size_t)P->ntx * P->ntp * sizeof(int4) : 0);
     L.state = take(ST_NSTATE * sizeof(double));
     L.hist = take((size_t)P->hist_cap * 2 * sizeof(double));
     L.lost = take(P->nlost * sizeof(double));
@@ -351,6 +354,7 @@ FusedArgs<T> fused_args(vp_sim *s, const void *src, void *dst)
         a.smax_in = from0 ? m0 : m1;
         a.smax_out = from0 ? m1 : m0;
     }
+    a.tile_src = P.fel ? nullptr : s->ptr<int4>(P.L.tsrc);
     a.csx = s->ptr<double2>(P.L.csx);
     a.tile_lost = s->ptr<double>(P.L.lost);
     a.tile_part = s->ptr<double>(P.L.part);
@@ -641,6 +645,9 @@ vp_status vp_create(const vp_grid *grid, int32_t basis, const vp_pusher *pusher,
         e = cudaMemcpyAsync(s->ws + P.L.piv, piv.data(), piv.size() * sizeof(double),
                             cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->ws + P.L.err, 0, sizeof(unsigned), s->stream);
+    // tile source rectangles not computed yet (each entry 0x80808080 = kTileSrcUnset)
+    if (e == cudaSuccess && P.kernel == VP_KERNEL_FUSED && !P.fel)
+        e = cudaMemsetAsync(s->ws + P.L.tsrc, 0x80, (size_t)P.ntx * P.ntp * sizeof(int4), s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cleanup(cuda_fail(nullptr, e, "table upload"));
     *out = s;

@@ -720,7 +720,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
     constexpr int R = (BASIS == VP_BASIS_TENT) ? 1 : 2;
     T *win = reinterpret_cast<T *>(smem_raw);
     T *gcol = win + (size_t)A.ws * (A.tp + 2 * A.Gp);   // [GRows][blockDim] column buffer (Galerkin)
-    __shared__ int s_ia, s_ib, s_ja, s_jb, s_smax, s_omax;
+    __shared__ int s_ia, s_ib, s_ja, s_jb, s_smax, s_omax, s_cached;
     __shared__ double s_r4[4][kFusedMaxThreads / 32];
     // Thomas pivots of tridiag(1/6, 2/3, 1/6) in T: entry kPivots holds the limit
     __shared__ T piv_cp[kPivots + 1], piv_ib[kPivots + 1];
@@ -762,10 +762,12 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
     if (GAL && A.fel_partials)
         for (int k = tid; k < TPe; k += blockDim.x) sig_s[k] = (T)A.sigma[P0 + k];
     if (tid == 0) {
-        s_ia = 0x7fffffff;
-        s_ib = -0x7fffffff;
-        s_ja = 0x7fffffff;
-        s_jb = -0x7fffffff;
+        const int4 e = A.tile_src ? A.tile_src[tile] : make_int4(kTileSrcUnset, 0, 0, 0);
+        s_cached = e.x != kTileSrcUnset;
+        s_ia = s_cached ? e.x : 0x7fffffff;
+        s_ib = s_cached ? e.y : -0x7fffffff;
+        s_ja = s_cached ? e.z : 0x7fffffff;
+        s_jb = s_cached ? e.w : -0x7fffffff;
         s_smax = 0;
         s_omax = 0;
     }
@@ -779,8 +781,10 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
     __syncthreads();
 
     // ---- bound the source nodes whose footprint can reach the widened tile (FP32 with
-    //      slack: every magnitude here is below 1e5 cells, where FP32 is exact to 1e-2)
-    {
+    //      slack: every magnitude here is below 1e5 cells, where FP32 is exact to 1e-2);
+    //      a push that does not change between steps gives the same bounds every step
+    const bool cached = s_cached != 0;
+    if (!cached) {
         const float SL = 0.05f;
         const float Mf = (float)M, phif = (float)phi;
         const float EU = fabsf((float)g.KU) * Mf, EV = fabsf((float)g.KV) * Mf;
@@ -856,6 +860,7 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
     }
     __syncthreads();
     const int ia = s_ia, ib = s_ib, ja = s_ja, jb = s_jb;
+    if (!cached && A.tile_src && tid == 0) A.tile_src[tile] = make_int4(ia, ib, ja, jb);
     double lost = 0.0;   // in the window's scaled units until the end of the tile
 
     // ---- FP32: fixed-point scale of the window from max|s| over the rows the walk reads, taken

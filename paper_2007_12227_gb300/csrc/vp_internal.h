@@ -117,7 +117,11 @@ struct FusedArgs {
     // [ntp][ntx]; it bounds the fixed-point window of the next step
     const float *smax_in;
     float *smax_out;
+    // source rectangle (ia, ib, ja, jb) per tile when the push does not change between steps
+    // (NULL for the FEL); entries equal to kTileSrcUnset are computed and stored by the tile
+    int4 *tile_src;
 };
+constexpr int kTileSrcUnset = (int)0x80808080;   // the bytes 0x80 (cudaMemset)
 
 // ---- launch entry points (defined in the .cu files) -----------------------
 cudaError_t build_tables(const Geometry &g, int precision, void *col, void *row,
