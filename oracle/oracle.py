@@ -40,7 +40,8 @@ class OrGrid(C.Structure):
 
 class OrPusher(C.Structure):
     _fields_ = [("kind", C.c_int), ("potential", C.c_int), ("v_sign", C.c_double),
-                ("omega", C.c_double), ("dt", C.c_double)]
+                ("omega", C.c_double), ("dt", C.c_double), ("delta", C.c_double),
+                ("sigma2", C.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -93,7 +94,7 @@ def _grid(g) -> OrGrid:
 
 def _pusher(pu) -> OrPusher:
     return OrPusher(int(pu.kind), int(pu.potential), float(pu.v_sign), float(pu.omega),
-                    float(pu.dt))
+                    float(pu.dt), float(getattr(pu, "delta", 0.0)), float(getattr(pu, "sigma2", 0.0)))
 
 
 def _arr(w, g) -> np.ndarray:

@@ -49,6 +49,8 @@ typedef struct {
     double v_sign;
     double omega;
     double dt;
+    double delta;   /* FEL detuning: d theta/dz = delta + eta */
+    double sigma2;  /* FEL space charge: kick amplitude A + i sigma2 <exp(-i theta)> */
 } or_pusher;
 
 enum { OR_KDK = 0, OR_ROT = 1, OR_FEL = 2 };
@@ -89,8 +91,12 @@ static double potential(const or_pusher *pu, double x)
  *       p_half = p - h/2 V'(x);  x' = x + h p_half;  p' = p_half - h/2 V'(x')
  *   exact rotation (linear oscillator advanced analytically, Sec. IV.A):
  *       phase advance omega h.
- *   FEL drift-kick-drift of d theta/dz = eta, d eta/dz = -(A e^{i theta} + cc)
- *   (Sec. IV.B with detuning and space charge set to zero), A = A^{n+1/2}.
+ *   FEL drift-kick-drift of the 1-D FEL equations (Sec. IV.B):
+ *       d theta/dz = delta + eta,  d eta/dz = -(K e^{i theta} + c.c.),
+ *   with the kick amplitude K = A + i sigma2 <exp(-i theta)> taken at the half
+ *   step by the caller (a_re, a_im = K):
+ *       th = theta + h/2 (delta + eta);  eta' = eta - 2 h Re(K e^{i th});
+ *       theta' = th + h/2 (delta + eta').
  */
 void or_push(const or_pusher *pu, double a_re, double a_im,
              double x, double p, double *xo, double *po)
@@ -107,11 +113,11 @@ void or_push(const or_pusher *pu, double a_re, double a_im,
         *xo = x * c + p * s / pu->omega;
         *po = -pu->omega * x * s + p * c;
     } else {
-        double th = x + 0.5 * h * p;
-        /* A e^{i th} + c.c. = 2 Re(A e^{i th}) */
+        double th = x + 0.5 * h * (pu->delta + p);
+        /* K e^{i th} + c.c. = 2 Re(K e^{i th}) */
         double re = a_re * cos(th) - a_im * sin(th);
         double pn = p - h * 2.0 * re;
-        *xo = th + 0.5 * h * pn;
+        *xo = th + 0.5 * h * (pu->delta + pn);
         *po = pn;
     }
 }
@@ -241,11 +247,32 @@ int or_step(const or_grid *g, int basis, int projection, const or_pusher *pu,
     const double hx = grid_hx(g), hp = grid_hp(g);
     const long n = (long)nx * np;
     double a_re = 0.0, a_im = 0.0;
+    double k_re = 0.0, k_im = 0.0;   /* kick amplitude */
     if (pu->kind == OR_FEL) {
         if (!fel) return 2;
         /* A^{n+1/2} = A^n + h/2 b^n */
         a_re = fel[0] + 0.5 * pu->dt * fel[2];
         a_im = fel[1] + 0.5 * pu->dt * fel[3];
+        k_re = a_re;
+        k_im = a_im;
+        if (pu->sigma2 != 0.0) {
+            /* space charge at the half step: the bunching of the weights at the
+             * half-drifted phases th = theta + h/2 (delta + eta); K = A^{n+1/2} + i sigma2 bt */
+            double s = 0.0, sc = 0.0, ss = 0.0;
+            for (int j = 0; j < np; ++j) {
+                const double p = g->p0 + j * hp;
+                for (int i = 0; i < nx; ++i) {
+                    const double w = w_in[(long)j * nx + i];
+                    const double th = g->x0 + i * hx + 0.5 * pu->dt * (pu->delta + p);
+                    s += w;
+                    sc += w * cos(th);
+                    ss += w * sin(th);
+                }
+            }
+            const double bt_re = sc / s, bt_im = -ss / s;
+            k_re = a_re - pu->sigma2 * bt_im;
+            k_im = a_im + pu->sigma2 * bt_re;
+        }
     }
     const double radius = (basis == OR_TENT) ? 1.0 : 2.0;
     double lost_acc = 0.0;
@@ -259,7 +286,7 @@ int or_step(const or_grid *g, int basis, int projection, const or_pusher *pu,
             if (w == 0.0) continue;
             const double x = g->x0 + i * hx;
             double xf, pf;
-            or_push(pu, a_re, a_im, x, p, &xf, &pf);
+            or_push(pu, k_re, k_im, x, p, &xf, &pf);
             const double u = (xf - g->x0) / hx;   /* pushed position, cell units */
             const double v = (pf - g->p0) / hp;
             const long c_lo = (long)ceil(u - radius), c_hi = (long)floor(u + radius);

@@ -93,6 +93,8 @@ class Pusher:
     dt: float = 0.05
     a0_re: float = 0.0         # FEL field amplitude at tau = 0
     a0_im: float = 0.0
+    delta: float = 0.0         # FEL detuning: d theta/dz = delta + p
+    sigma2: float = 0.0        # FEL space charge: kick amplitude A + i sigma2 <exp(-i theta)>
 
 
 @dataclass

@@ -376,14 +376,25 @@ def test_pendulum_trapped_mass_converges_with_grid():
 
 
 # ---------------------------------------------------------------------------------- FEL
-def _fel_root(sp):
-    """Growing root of lambda = int f0'(p) / (lambda + i p) dp, Gaussian f0 of spread sp."""
-    def disp(lam):
+def _fel_root(sp, delta=0.0, sigma2=0.0, lam=None):
+    """Growing root of the linearised FEL equations of Sec. IV.B for a Gaussian f0 of spread sp.
+
+    With f = f0(p) + f1(p) e^{i theta + lambda z}, A ~ e^{lambda z} and b = <e^{-i theta}>,
+    d theta/dz = delta + p and the kick amplitude A + i sigma2 b give
+    b = (A + i sigma2 b) J(lambda), J = int f0'(p) / (lambda + i (delta + p)) dp, and
+    dA/dz = b gives lambda A = b:  lambda (1 - i sigma2 J) = J.
+    """
+    def J(l):
         f = lambda p: -p / sp ** 2 * math.exp(-0.5 * (p / sp) ** 2) / (math.sqrt(2 * math.pi) * sp)
-        re = quad(lambda p: (f(p) / (lam + 1j * p)).real, -12 * sp, 12 * sp, limit=400)[0]
-        im = quad(lambda p: (f(p) / (lam + 1j * p)).imag, -12 * sp, 12 * sp, limit=400)[0]
-        return lam - (re + 1j * im)
-    lam = complex(CLOSED["fel_cold_beam_growth"]["lambda_re"], CLOSED["fel_cold_beam_growth"]["lambda_im"])
+        re = quad(lambda p: (f(p) / (l + 1j * (delta + p))).real, -12 * sp, 12 * sp, limit=400)[0]
+        im = quad(lambda p: (f(p) / (l + 1j * (delta + p))).imag, -12 * sp, 12 * sp, limit=400)[0]
+        return re + 1j * im
+
+    def disp(l):
+        j = J(l)
+        return l * (1 - 1j * sigma2 * j) - j
+    if lam is None:
+        lam = complex(CLOSED["fel_cold_beam_growth"]["lambda_re"], CLOSED["fel_cold_beam_growth"]["lambda_im"])
     for _ in range(50):
         d = disp(lam)
         e = 1e-7
@@ -418,6 +429,44 @@ def test_fel_linear_growth_rate_matches_warm_beam_theory():
     assert abs(slope - lam.real) < 5e-3 * lam.real
     assert lam.real < math.sqrt(3) / 2          # a warm beam grows slower than a cold one
     assert amp[-1] < math.log(0.01)
+
+
+def _cold_root(delta, sigma2):
+    """Cold beam (f0 = a delta function): J = i / (lambda + i delta)^2, so
+    lambda (lambda + i delta)^2 + sigma2 lambda - i = 0; the root of largest growth."""
+    r = np.roots([1.0, 2j * delta, sigma2 - delta ** 2, -1j])
+    return r[np.argmax(r.real)]
+
+
+@pytest.mark.parametrize("delta,sigma2", [(0.3, 0.2), (-0.4, 0.1), (0.0, 0.3)])
+def test_fel_dispersion_with_detuning_and_space_charge_cold_limit(delta, sigma2):
+    """The warm-beam relation reduces to the cold-beam cubic as the energy spread vanishes."""
+    c = _cold_root(delta, sigma2)
+    lam = _fel_root(1e-3, delta, sigma2, lam=c)
+    assert abs(lam - c) < 2e-3
+    # space charge slows the growth, and so does detuning from resonance
+    assert c.real < math.sqrt(3) / 2
+
+
+@pytest.mark.parametrize("delta,sigma2", [(0.3, 0.2), (-0.4, 0.1), (0.0, 0.3)])
+def test_fel_growth_with_detuning_and_space_charge_matches_theory(delta, sigma2):
+    """Full FEL model of Sec. IV.B: ln|A| grows at Re(lambda) and the phase of A turns at
+    Im(lambda) of the warm-beam relation with detuning delta and space charge sigma2."""
+    sp = 0.05
+    g = I.Grid(32, 256, 0.0, 2 * math.pi, -0.5, 0.5)
+    pu = I.Pusher(I.PUSH_FEL, I.POT_FREE, 1.0, 1.0, 0.01, 1e-6, 0.0, delta, sigma2)
+    wl = I.Workload("t", g, pu, I.BASIS_CUBIC, I.FP64, 0, "fel_gaussian", dict(sp=sp, eps=1e-6))
+    st = O.State(g, pu, O.CUBIC, O.GALERKIN, I.make_f0(wl))
+    nst = 1000
+    hist = st.run(nst, history=True)
+    tau = (np.arange(nst) + 1) * pu.dt
+    a = hist[:, 0] + 1j * hist[:, 1]
+    sel = (tau >= 5.0) & (tau <= 10.0)
+    growth = np.polyfit(tau[sel], np.log(np.abs(a[sel])), 1)[0]
+    turn = np.polyfit(tau[sel], np.unwrap(np.angle(a[sel])), 1)[0]
+    lam = _fel_root(sp, delta, sigma2, lam=_cold_root(delta, sigma2))
+    assert abs(growth - lam.real) < 5e-3 * lam.real
+    assert abs(turn - lam.imag) < 5e-3 * max(1.0, abs(lam.imag))
 
 
 def test_fel_energy_invariant_drift_is_second_order():
