@@ -93,6 +93,12 @@ typedef struct vp_pusher {
     double omega;          /* harmonic frequency */
     double dt;             /* step h */
     double a0_re, a0_im;   /* FEL: field amplitude A at tau = 0 */
+    /* FEL model of Sec. IV.B in full: d theta/dz = delta + eta and the kick
+     * amplitude A + i sigma2 <exp(-i theta)> (space charge), taken at the
+     * half-drifted phases of each step. 0, 0: the universal-scaling model.
+     * Batches and the server take sigma2 = 0 only (VP_ERR_UNSUPPORTED). */
+    double delta;
+    double sigma2;
 } vp_pusher;
 
 typedef struct vp_opts {

@@ -28,8 +28,8 @@ constexpr int kMoutLen = 32;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t f0, f1, tmp, col, row, rowb, vcb, rowbf, vcbf, csx, ucol, vcol, piv, sigma, smax, tsrc, state,
-        hist,
+    size_t f0, f1, tmp, col, row, rowb, vcb, rowbf, vcbf, csx, ucol, vcol, piv, sigma, smax, tsrc, rtil,
+        state, hist,
         lost, part, mpart, mout, err, total;
 };
 
@@ -75,7 +75,7 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     if (pu->potential < 0 || pu->potential > 2)
         return fail(msg, VP_ERR_ARG, "unknown potential %d", pu->potential);
     if (!finite(pu->dt) || !finite(pu->v_sign) || !finite(pu->omega) || !finite(pu->a0_re) ||
-        !finite(pu->a0_im))
+        !finite(pu->a0_im) || !finite(pu->delta) || !finite(pu->sigma2))
         return fail(msg, VP_ERR_ARG, "pusher parameters must be finite");
     if (opts->precision != VP_FP32 && opts->precision != VP_FP64)
         return fail(msg, VP_ERR_ARG, "unknown precision %d", opts->precision);
@@ -102,6 +102,8 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     g.v_sign = pu->v_sign;
     g.omega = pu->omega;
     g.dt = pu->dt;
+    g.delta = pu->kind == VP_PUSH_FEL_DKD ? pu->delta : 0.0;
+    g.sigma2 = pu->kind == VP_PUSH_FEL_DKD ? pu->sigma2 : 0.0;
     const double h = pu->dt;
     const bool pend = pu->kind == VP_PUSH_LEAPFROG_KDK && pu->potential == VP_POT_PENDULUM;
     P->fel = pu->kind == VP_PUSH_FEL_DKD;
@@ -241,6 +243,8 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     L.sigma = take(grid->np * sizeof(double));
     // FP32 one-pass plans: max|s| per tile of each state buffer (the fixed-point window scale)
     L.smax = take(kernel == VP_KERNEL_FUSED && sz == 4 ? 2 * (size_t)P->ntx * P->ntp * sizeof(float) : 0);
+    // FEL space charge: half-drift row factors (cos, sin) for the stored state
+    L.rtil = take(P->fel && g.sigma2 != 0.0 ? 2 * (size_t)grid->np * sizeof(double) : 0);
     // one-pass plans of a push fixed for the whole run: each tile's source rectangle
     L.tsrc = take(kernel == VP_KERNEL_FUSED && !P->fel ? (size_t)P->ntx * P->ntp * sizeof(int4) : 0);
     L.state = take(ST_NSTATE * sizeof(double));
@@ -401,6 +405,21 @@ vp_status fel_bunching(vp_sim *s, const void *w, int init)
     return VP_OK;
 }
 
+// FEL space charge: K = A^{n+1/2} + i sigma2 <e^{-i theta~}> over the stored state st
+template <typename T>
+vp_status fel_space_charge(vp_sim *s, const void *st)
+{
+    const Plan &P = s->P;
+    const double *rt = s->ptr<double>(P.L.rtil);
+    double *part = s->ptr<double>(P.L.part);
+    VP_CUDA(s, launch_fel_tilde<T>(static_cast<const T *>(st), P.g.nx, P.g.np, s->ptr<double2>(P.L.csx),
+                                   rt, rt + P.g.np, P.state_s ? s->ptr<double>(P.L.sigma) : nullptr, part,
+                                   s->stream));
+    VP_CUDA(s, launch_fel_kick(part, fel_partial_blocks(P.g.nx, P.g.np), s->ptr<double>(P.L.state),
+                               P.g.sigma2, s->stream));
+    return VP_OK;
+}
+
 // ev (optional): VP_NPHASES + 1 events per step, recorded at the phase boundaries
 template <typename T>
 vp_status do_steps(vp_sim *s, int n, cudaEvent_t *ev = nullptr)
@@ -453,6 +472,10 @@ vp_status do_steps(vp_sim *s, int n, cudaEvent_t *ev = nullptr)
         if (P.fel) {
             VP_CUDA(s, launch_fel_finalize(part, nparts, state, s->ptr<double>(P.L.hist), P.hist_cap,
                                            P.g.dt, 0, s->stream));
+            if (P.g.sigma2 != 0.0) {
+                const vp_status sc = fel_space_charge<T>(s, dst);
+                if (sc != VP_OK) return sc;
+            }
         } else {
             VP_CUDA(s, launch_count_step(state, P.g.dt, s->stream));
         }
@@ -622,6 +645,28 @@ vp_status vp_create(const vp_grid *grid, int32_t basis, const vp_pusher *pusher,
         }
         for (int j = g.np - 2; j >= 0; --j) sigma[j] -= cpv[j] * sigma[j + 1];
     }
+    // FEL space charge: cos and sin of the half drift h/2 (delta + p_j), times Lambda_p^{-1}
+    // (symmetric) when the stored state is s = Lambda_p w, so that sum_j w_ij f_j = sum_j s_ij rf_j
+    std::vector<double> rtil;
+    if (P.fel && g.sigma2 != 0.0) {
+        rtil.resize(2 * (size_t)g.np);
+        for (int j = 0; j < g.np; ++j) {
+            const double ph = 0.5 * g.dt * (g.delta + g.p0 + j * g.hp);
+            rtil[j] = cos(ph);
+            rtil[g.np + j] = sin(ph);
+        }
+        if (P.state_s)
+            for (int q = 0; q < 2; ++q) {
+                double *v = rtil.data() + (size_t)q * g.np;
+                double beta = 2.0 / 3.0;
+                v[0] /= beta;
+                for (int j = 1; j < g.np; ++j) {
+                    beta = 2.0 / 3.0 - (1.0 / 6.0) * cpv[j - 1];
+                    v[j] = (v[j] - (1.0 / 6.0) * v[j - 1]) / beta;
+                }
+                for (int j = g.np - 2; j >= 0; --j) v[j] -= cpv[j] * v[j + 1];
+            }
+    }
     // FP32 copies of the bound tables for the one-pass kernel's tile bounds
     std::vector<float4> rowbf(g.np);
     for (int j = 0; j < g.np; ++j)
@@ -635,6 +680,12 @@ vp_status vp_create(const vp_grid *grid, int32_t basis, const vp_pusher *pusher,
                             cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cleanup(cuda_fail(nullptr, e, "bound table upload"));
+    if (!rtil.empty()) {
+        e = cudaMemcpyAsync(s->ws + P.L.rtil, rtil.data(), rtil.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return cleanup(cuda_fail(nullptr, e, "space-charge table upload"));
+    }
     e = cudaMemcpyAsync(s->ws + P.L.sigma, sigma.data(), sigma.size() * sizeof(double),
                         cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
@@ -702,6 +753,11 @@ static vp_status set_f_common(vp_sim *s, const void *src, int32_t dtype, size_t 
             VP_CUDA(s, launch_lambda_p_mul<float>(static_cast<const float *>(dst),
                                                   static_cast<float *>(s->f(0)), P.g.nx, P.g.np,
                                                   s->stream));
+    }
+    if (P.fel && P.g.sigma2 != 0.0) {
+        const vp_status sc = P.precision == VP_FP64 ? fel_space_charge<double>(s, s->f(0))
+                                                    : fel_space_charge<float>(s, s->f(0));
+        if (sc != VP_OK) return sc;
     }
     if (P.kernel == VP_KERNEL_FUSED && P.precision == VP_FP32)
         VP_CUDA(s, launch_tile_max(static_cast<const float *>(s->f(0)), s->ptr<float>(P.L.smax), P.g.nx,
@@ -994,6 +1050,8 @@ vp_status batch_layout(vp_sim *const *sims, int count, BatchLayout *L, int *nite
             return fail(msg, VP_ERR_UNSUPPORTED, "batches hold FP32 simulations (simulation %d)", k);
         if (P.g.basis != P0.g.basis || P.g.projection != P0.g.projection)
             return fail(msg, VP_ERR_ARG, "simulation %d differs in basis or projection", k);
+        if (P.g.sigma2 != 0.0)
+            return fail(msg, VP_ERR_UNSUPPORTED, "simulation %d has FEL space charge (sigma2 != 0)", k);
         items += P.ntx * P.ntp;
     }
     batch_layout_of(count, items, L);

@@ -773,8 +773,8 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
     }
     double al = g.alpha0, be = g.beta0, M = g.m0, phi = g.phi0;
     if (g.kind == VP_PUSH_FEL_DKD) {
-        al = -A.state[ST_AH_IM];
-        be = A.state[ST_AH_RE];
+        al = -A.state[ST_K_IM];
+        be = A.state[ST_K_RE];
         M = A.state[ST_M];
         phi = A.state[ST_PHI];
     }

@@ -44,7 +44,8 @@ struct RowBound {
 // Device FEL / step state (doubles).
 enum {
     ST_A_RE = 0, ST_A_IM, ST_B_RE, ST_B_IM, ST_AH_RE, ST_AH_IM, ST_TAU, ST_STEP,
-    ST_M, ST_PHI,   // |A^{n+1/2}| and atan2(Re A, -Im A): amplitude and phase of the sine term
+    ST_M, ST_PHI,   // |K| and atan2(Re K, -Im K): amplitude and phase of the sine term
+    ST_K_RE, ST_K_IM,   // FEL kick amplitude K = A^{n+1/2} + i sigma2 <exp(-i theta~)>
     ST_NSTATE = 16
 };
 
@@ -59,6 +60,7 @@ struct Geometry {
     double x0, x1, p0, p1, hx, hp;
     int basis, kind, potential, projection;
     double v_sign, omega, dt;
+    double delta, sigma2;   // FEL detuning and space-charge coefficient
     double KU, KV;          // coefficients of the sine term
     double alpha0, beta0;   // sine-term weights for non-FEL pushers
     double m0, phi0;        // hypot(alpha0, beta0), atan2(beta0, alpha0)
@@ -183,6 +185,14 @@ template <typename T>
 cudaError_t launch_fel_partials(const T *w, int nx, int np, const double2 *csx, double *part,
                                 cudaStream_t s);
 int fel_partial_blocks(int nx, int np);
+// FEL space charge: per-block sums of the state against the half-drift row factors
+// (rc, rs: cos and sin of h/2 (delta + p_j), times Lambda_p^{-1} when the state is s) and
+// the mass weights (sig, NULL = 1), then K = A^{n+1/2} + i sigma2 <exp(-i theta~)>
+template <typename T>
+cudaError_t launch_fel_tilde(const T *state, int nx, int np, const double2 *csx, const double *rc,
+                             const double *rs, const double *sig, double *part, cudaStream_t s);
+cudaError_t launch_fel_kick(const double *part, int nparts, double *state, double sigma2,
+                            cudaStream_t s);
 cudaError_t launch_fel_finalize(const double *part, int nparts, double *state, double *hist,
                                 int hist_cap, double dt, int init, cudaStream_t s);
 cudaError_t launch_count_step(double *state, double dt, cudaStream_t s);

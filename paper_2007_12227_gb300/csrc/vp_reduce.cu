@@ -58,6 +58,78 @@ __global__ void fel_partials_kernel(const T *__restrict__ w, int nx, int np,
     }
 }
 
+// FEL space charge: per block (32 columns x kFelRows rows) the sums of the state against the
+// mass weights and against the half-drift phase factors e^{-i (theta_i + phi_j)}:
+// per column C = sum_j s_ij rc_j, S = sum_j s_ij rs_j, then Re += cos(th) C - sin(th) S and
+// Im -= sin(th) C + cos(th) S (rc, rs already carry Lambda_p^{-1} for the state s = Lambda_p w)
+template <typename T>
+__global__ void fel_tilde_kernel(const T *__restrict__ st, int nx, int np, const double2 *__restrict__ csx,
+                                 const double *__restrict__ rc, const double *__restrict__ rs,
+                                 const double *__restrict__ sig, double *part)
+{
+    __shared__ double s_red[3][kRedThreads / 32];
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const int col = blockIdx.x * 32 + lane;
+    const int r0 = blockIdx.y * kFelRows;
+    const int r1 = min(r0 + kFelRows, np);
+    double m = 0.0, c = 0.0, sn = 0.0;
+    if (col < nx)
+        for (int r = r0 + wy; r < r1; r += kRedThreads / 32) {
+            const double v = (double)st[(size_t)r * nx + col];
+            m += v * (sig ? sig[r] : 1.0);
+            c += v * rc[r];
+            sn += v * rs[r];
+        }
+    double v3[3] = {m, 0.0, 0.0};
+    if (col < nx) {
+        const double2 t = csx[col];
+        v3[1] = t.x * c - t.y * sn;
+        v3[2] = -(t.y * c + t.x * sn);
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        for (int o = 16; o > 0; o >>= 1) v3[q] += __shfl_down_sync(0xffffffffu, v3[q], o);
+        if (lane == 0) s_red[q][wy] = v3[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+        for (int q = 0; q < 3; ++q) {
+            double t = 0.0;
+            for (int k = 0; k < kRedThreads / 32; ++k) t += s_red[q][k];
+            part[3 * b + q] = t;
+        }
+    }
+}
+
+// K = A^{n+1/2} + i sigma2 bt, bt = <e^{-i theta~}> from the tilde partial sums (one block)
+__global__ void fel_kick_kernel(const double *__restrict__ part, int nparts, double *state, double sigma2)
+{
+    __shared__ double s[3][kRedThreads];
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int k = threadIdx.x; k < nparts; k += blockDim.x) {
+        a0 += part[3 * k];
+        a1 += part[3 * k + 1];
+        a2 += part[3 * k + 2];
+    }
+    s[0][threadIdx.x] = a0;
+    s[1][threadIdx.x] = a1;
+    s[2][threadIdx.x] = a2;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int q = 0; q < 3; ++q) s[q][threadIdx.x] += s[q][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    const double bt_re = s[1][0] / s[0][0], bt_im = s[2][0] / s[0][0];
+    const double kr = state[ST_AH_RE] - sigma2 * bt_im, ki = state[ST_AH_IM] + sigma2 * bt_re;
+    state[ST_K_RE] = kr;
+    state[ST_K_IM] = ki;
+    state[ST_M] = hypot(kr, ki);
+    state[ST_PHI] = atan2(kr, -ki);
+}
+
 // FEL field update from per-block partial sums (run by one block)
 __device__ void fel_finalize_block(const double *__restrict__ part, int nparts, double *state,
                                    double *hist, int hist_cap, double dt, int init)
@@ -87,6 +159,9 @@ __device__ void fel_finalize_block(const double *__restrict__ part, int nparts, 
         // A^0 already stored; A^{1/2} = A^0 + h/2 b^0
         state[ST_AH_RE] = state[ST_A_RE] + 0.5 * dt * b_re;
         state[ST_AH_IM] = state[ST_A_IM] + 0.5 * dt * b_im;
+        // kick amplitude K = A^{1/2} (space charge adds i sigma2 <e^{-i theta~}> afterwards)
+        state[ST_K_RE] = state[ST_AH_RE];
+        state[ST_K_IM] = state[ST_AH_IM];
         state[ST_M] = hypot(state[ST_AH_RE], state[ST_AH_IM]);
         state[ST_PHI] = atan2(state[ST_AH_RE], -state[ST_AH_IM]);
         return;
@@ -97,7 +172,9 @@ __device__ void fel_finalize_block(const double *__restrict__ part, int nparts, 
     state[ST_A_IM] = aim;
     state[ST_AH_RE] = are + 0.5 * dt * b_re;
     state[ST_AH_IM] = aim + 0.5 * dt * b_im;
-    // sine-term weights of the next push: alpha = -Im A, beta = Re A
+    state[ST_K_RE] = state[ST_AH_RE];
+    state[ST_K_IM] = state[ST_AH_IM];
+    // sine-term weights of the next push: alpha = -Im K, beta = Re K
     state[ST_M] = hypot(state[ST_AH_RE], state[ST_AH_IM]);
     state[ST_PHI] = atan2(state[ST_AH_RE], -state[ST_AH_IM]);
     const long step = (long)state[ST_STEP];
@@ -231,6 +308,25 @@ __global__ void convert_kernel(const Tin *__restrict__ in, Tout *__restrict__ ou
 int fel_partial_blocks(int nx, int np)
 {
     return ((nx + 31) / 32) * ((np + kFelRows - 1) / kFelRows);
+}
+
+template <typename T>
+cudaError_t launch_fel_tilde(const T *state, int nx, int np, const double2 *csx, const double *rc,
+                             const double *rs, const double *sig, double *part, cudaStream_t s)
+{
+    dim3 grid((nx + 31) / 32, (np + kFelRows - 1) / kFelRows);
+    fel_tilde_kernel<T><<<grid, kRedThreads, 0, s>>>(state, nx, np, csx, rc, rs, sig, part);
+    return cudaGetLastError();
+}
+template cudaError_t launch_fel_tilde<float>(const float *, int, int, const double2 *, const double *,
+                                             const double *, const double *, double *, cudaStream_t);
+template cudaError_t launch_fel_tilde<double>(const double *, int, int, const double2 *, const double *,
+                                              const double *, const double *, double *, cudaStream_t);
+
+cudaError_t launch_fel_kick(const double *part, int nparts, double *state, double sigma2, cudaStream_t s)
+{
+    fel_kick_kernel<<<1, kRedThreads, 0, s>>>(part, nparts, state, sigma2);
+    return cudaGetLastError();
 }
 
 template <typename T>

@@ -125,8 +125,8 @@ __global__ void __launch_bounds__(kThreads) step_tiled_kernel(const StepArgs<T> 
 
     double al = g.alpha0, be = g.beta0, M = g.m0, phi = g.phi0;
     if (g.kind == VP_PUSH_FEL_DKD) {
-        al = -A.state[ST_AH_IM];
-        be = A.state[ST_AH_RE];
+        al = -A.state[ST_K_IM];
+        be = A.state[ST_K_RE];
         M = A.state[ST_M];
         phi = A.state[ST_PHI];
     }
@@ -316,8 +316,8 @@ __global__ void __launch_bounds__(kThreads) step_scatter_kernel(const StepArgs<T
     const int nx = g.nx, np = g.np;
     double al = g.alpha0, be = g.beta0;
     if (g.kind == VP_PUSH_FEL_DKD) {
-        al = -A.state[ST_AH_IM];
-        be = A.state[ST_AH_RE];
+        al = -A.state[ST_K_IM];
+        be = A.state[ST_K_RE];
     }
     const T alT = (T)al, beT = (T)be, KUT = (T)g.KU, KVT = (T)g.KV;
     double lost = 0.0;

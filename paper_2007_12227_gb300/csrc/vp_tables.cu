@@ -89,8 +89,9 @@ __global__ void row_kernel(Geometry g, RowEntry<T> *row, RowBound *rowb)
         U = p * sin(th) / (g.omega * g.hx);
         V = p * (cos(th) - 1.0) / g.hp;
     } else {
-        U = (h / g.hx) * p;
-        y = 0.5 * h * p;
+        // FEL: d theta/dz = delta + p; the kick phase is taken after the first half drift
+        U = (h / g.hx) * (p + g.delta);
+        y = 0.5 * h * (p + g.delta);
     }
     RowEntry<T> e;
     double f;

@@ -33,7 +33,7 @@ class vp_grid(C.Structure):
 class vp_pusher(C.Structure):
     _fields_ = [("kind", C.c_int32), ("potential", C.c_int32), ("v_sign", C.c_double),
                 ("omega", C.c_double), ("dt", C.c_double), ("a0_re", C.c_double),
-                ("a0_im", C.c_double)]
+                ("a0_im", C.c_double), ("delta", C.c_double), ("sigma2", C.c_double)]
 
 
 class vp_opts(C.Structure):
@@ -182,7 +182,8 @@ def make_grid(g) -> vp_grid:
 
 def make_pusher(p) -> vp_pusher:
     return vp_pusher(int(p.kind), int(p.potential), float(p.v_sign), float(p.omega), float(p.dt),
-                     float(p.a0_re), float(p.a0_im))
+                     float(p.a0_re), float(p.a0_im), float(getattr(p, "delta", 0.0)),
+                     float(getattr(p, "sigma2", 0.0)))
 
 
 def vp_workspace_size(grid, basis, pusher, opts) -> int:
