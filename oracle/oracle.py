@@ -24,7 +24,7 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-KDK, ROTATION, FEL = 0, 1, 2
+KDK, ROTATION, FEL, FEL_RK4 = 0, 1, 2, 3
 FREE, PENDULUM, HARMONIC = 0, 1, 2
 TENT, CUBIC = 0, 1
 GALERKIN, LUMPED = 0, 1
@@ -112,7 +112,7 @@ class State:
         self.fel = np.zeros(4, dtype=np.float64)
         self.lost = np.zeros(1, dtype=np.float64)
         self.step_count = 0
-        if pusher.kind == FEL:
+        if pusher.kind in (FEL, FEL_RK4):
             self.fel[0], self.fel[1] = pusher.a0_re, pusher.a0_im
             br, bi = bunching(grid, self.w)
             self.fel[2], self.fel[3] = br, bi

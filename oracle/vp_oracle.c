@@ -44,7 +44,7 @@ typedef struct {
 } or_grid;
 
 typedef struct {
-    int kind;       /* 0 leapfrog KDK, 1 exact rotation, 2 FEL DKD */
+    int kind;       /* 0 leapfrog KDK, 1 exact rotation, 2 FEL DKD, 3 FEL RK4 */
     int potential;  /* 0 free, 1 pendulum V=-s cos x, 2 harmonic V=w^2 x^2/2 */
     double v_sign;
     double omega;
@@ -53,7 +53,7 @@ typedef struct {
     double sigma2;  /* FEL space charge: kick amplitude A + i sigma2 <exp(-i theta)> */
 } or_pusher;
 
-enum { OR_KDK = 0, OR_ROT = 1, OR_FEL = 2 };
+enum { OR_KDK = 0, OR_ROT = 1, OR_FEL = 2, OR_FEL_RK4 = 3 };
 enum { OR_FREE = 0, OR_PEND = 1, OR_HARM = 2 };
 enum { OR_TENT = 0, OR_CUBIC = 1 };
 enum { OR_GALERKIN = 0, OR_LUMPED = 1 };
@@ -119,6 +119,35 @@ void or_push(const or_pusher *pu, double a_re, double a_im,
         double pn = p - h * 2.0 * re;
         *xo = th + 0.5 * h * (pu->delta + pn);
         *po = pn;
+    }
+}
+
+/*
+ * FEL, classical fourth-order Runge-Kutta (the integrator of Sec. IV.B) for one particle of the
+ * system d theta/dz = delta + eta, d eta/dz = -(K e^{i theta} + c.c.), given the kick amplitudes
+ * K_1..K_4 of the four stages (k[2 s], k[2 s + 1]: re, im of stage s), which the caller forms from
+ * A and the stage bunchings. th_s, p_s (may be NULL): the stage positions, s = 0..3.
+ */
+void or_push_rk4(const or_pusher *pu, const double *k, double x, double p, double *xo, double *po,
+                 double *th_s, double *p_s)
+{
+    const double h = pu->dt, d = pu->delta;
+    double th[4], pp[4], dp[4];
+    th[0] = x;
+    pp[0] = p;
+    for (int s = 0; s < 4; ++s) {
+        if (s > 0) {
+            const double c = (s == 3) ? h : 0.5 * h;
+            th[s] = x + c * (d + pp[s - 1]);
+            pp[s] = p + c * dp[s - 1];
+        }
+        dp[s] = -2.0 * (k[2 * s] * cos(th[s]) - k[2 * s + 1] * sin(th[s]));
+    }
+    *xo = x + h / 6.0 * ((d + pp[0]) + 2.0 * (d + pp[1]) + 2.0 * (d + pp[2]) + (d + pp[3]));
+    *po = p + h / 6.0 * (dp[0] + 2.0 * dp[1] + 2.0 * dp[2] + dp[3]);
+    for (int s = 0; s < 4; ++s) {
+        if (th_s) th_s[s] = th[s];
+        if (p_s) p_s[s] = pp[s];
     }
 }
 
@@ -274,6 +303,39 @@ int or_step(const or_grid *g, int basis, int projection, const or_pusher *pu,
             k_im = a_im + pu->sigma2 * bt_re;
         }
     }
+    /* RK4 (Sec. IV.B): stage s needs the bunching b_s of all particles at their stage-s phases,
+     * which depend on the amplitudes of the earlier stages: A_1 = A, A_2 = A + h/2 b_1,
+     * A_3 = A + h/2 b_2, A_4 = A + h b_3, K_s = A_s + i sigma2 b_s, and
+     * A' = A + h/6 (b_1 + 2 b_2 + 2 b_3 + b_4). */
+    double rk[8] = {0}, a_new_re = 0.0, a_new_im = 0.0;
+    if (pu->kind == OR_FEL_RK4) {
+        if (!fel) return 2;
+        const double h = pu->dt;
+        double b[8];
+        for (int s = 0; s < 4; ++s) {
+            double sw = 0.0, sc = 0.0, ss = 0.0;
+            for (int j = 0; j < np; ++j) {
+                const double p = g->p0 + j * hp;
+                for (int i = 0; i < nx; ++i) {
+                    const double w = w_in[(long)j * nx + i];
+                    double th[4], xo, po;
+                    or_push_rk4(pu, rk, g->x0 + i * hx, p, &xo, &po, th, NULL);
+                    sw += w;
+                    sc += w * cos(th[s]);
+                    ss += w * sin(th[s]);
+                }
+            }
+            b[2 * s] = sc / sw;
+            b[2 * s + 1] = -ss / sw;
+            const double c = (s == 0) ? 0.0 : (s == 3 ? h : 0.5 * h);
+            const double ar = fel[0] + (s == 0 ? 0.0 : c * b[2 * (s - 1)]);
+            const double ai = fel[1] + (s == 0 ? 0.0 : c * b[2 * (s - 1) + 1]);
+            rk[2 * s] = ar - pu->sigma2 * b[2 * s + 1];
+            rk[2 * s + 1] = ai + pu->sigma2 * b[2 * s];
+        }
+        a_new_re = fel[0] + h / 6.0 * (b[0] + 2.0 * b[2] + 2.0 * b[4] + b[6]);
+        a_new_im = fel[1] + h / 6.0 * (b[1] + 2.0 * b[3] + 2.0 * b[5] + b[7]);
+    }
     const double radius = (basis == OR_TENT) ? 1.0 : 2.0;
     double lost_acc = 0.0;
     memset(w_out, 0, sizeof(double) * n);
@@ -286,7 +348,10 @@ int or_step(const or_grid *g, int basis, int projection, const or_pusher *pu,
             if (w == 0.0) continue;
             const double x = g->x0 + i * hx;
             double xf, pf;
-            or_push(pu, k_re, k_im, x, p, &xf, &pf);
+            if (pu->kind == OR_FEL_RK4)
+                or_push_rk4(pu, rk, x, p, &xf, &pf, NULL, NULL);
+            else
+                or_push(pu, k_re, k_im, x, p, &xf, &pf);
             const double u = (xf - g->x0) / hx;   /* pushed position, cell units */
             const double v = (pf - g->p0) / hp;
             const long c_lo = (long)ceil(u - radius), c_hi = (long)floor(u + radius);
@@ -315,8 +380,8 @@ int or_step(const or_grid *g, int basis, int projection, const or_pusher *pu,
     }
     if (lost) *lost += lost_acc / (hx * hp);
 
-    if (pu->kind == OR_FEL) {
-        /* b = <exp(-i theta)> over the new weights; A^{n+1} = A^{n+1/2} + h/2 b */
+    if (pu->kind == OR_FEL || pu->kind == OR_FEL_RK4) {
+        /* b = <exp(-i theta)> over the new weights; DKD: A^{n+1} = A^{n+1/2} + h/2 b */
         double s = 0.0, sc = 0.0, ss = 0.0;
         for (int j = 0; j < np; ++j)
             for (int i = 0; i < nx; ++i) {
@@ -328,8 +393,13 @@ int or_step(const or_grid *g, int basis, int projection, const or_pusher *pu,
             }
         fel[2] = sc / s;
         fel[3] = -ss / s;
-        fel[0] = a_re + 0.5 * pu->dt * fel[2];
-        fel[1] = a_im + 0.5 * pu->dt * fel[3];
+        if (pu->kind == OR_FEL_RK4) {
+            fel[0] = a_new_re;
+            fel[1] = a_new_im;
+        } else {
+            fel[0] = a_re + 0.5 * pu->dt * fel[2];
+            fel[1] = a_im + 0.5 * pu->dt * fel[3];
+        }
     }
     return 0;
 }
@@ -365,7 +435,7 @@ int or_run(const or_grid *g, int basis, int projection, const or_pusher *pu,
         int rc = or_step(g, basis, projection, pu, fel, w, tmp, lost);
         if (rc) { free(tmp); return rc; }
         memcpy(w, tmp, sizeof(double) * n);
-        if (hist && pu->kind == OR_FEL) {
+        if (hist && (pu->kind == OR_FEL || pu->kind == OR_FEL_RK4)) {
             hist[2 * s] = fel[0];
             hist[2 * s + 1] = fel[1];
         }
@@ -422,7 +492,7 @@ void or_moments(const or_grid *g, const or_pusher *pu, const double *w,
     out[4] = sxx / s - mx * mx;
     out[5] = spp / s - mp * mp;
     out[6] = sxp / s - mx * mp;
-    if (pu->kind == OR_FEL)
+    if ((pu->kind == OR_FEL || pu->kind == OR_FEL_RK4))
         out[7] = mp + (a ? a[0] * a[0] + a[1] * a[1] : 0.0);
     else
         out[7] = sh / s;

@@ -20,7 +20,7 @@ import numpy as np
 
 # enum values mirror include/vlasov.h
 BASIS_TENT, BASIS_CUBIC = 0, 1
-PUSH_KDK, PUSH_ROTATION, PUSH_FEL = 0, 1, 2
+PUSH_KDK, PUSH_ROTATION, PUSH_FEL, PUSH_FEL_RK4 = 0, 1, 2, 3
 POT_FREE, POT_PENDULUM, POT_HARMONIC = 0, 1, 2
 FP32, FP64 = 0, 1
 PROJ_GALERKIN, PROJ_LUMPED = 0, 1

@@ -469,6 +469,55 @@ def test_fel_growth_with_detuning_and_space_charge_matches_theory(delta, sigma2)
     assert abs(turn - lam.imag) < 5e-3 * max(1.0, abs(lam.imag))
 
 
+def _energy_drifts(kind, dts, sigma2=0.0):
+    """|change of <p> + |A|^2| over tau = 1 (no weight leaves the momentum range)."""
+    out = []
+    for dt in dts:
+        g = I.Grid(64, 256, 0.0, 2 * math.pi, -2.5, 2.5)
+        pu = I.Pusher(kind, I.POT_FREE, 1.0, 1.0, dt, 0.3, 0.0, 0.0, sigma2)
+        wl = I.Workload("t", g, pu, I.BASIS_CUBIC, I.FP64, 0, "fel_gaussian", dict(sp=0.1, eps=1e-2))
+        st = O.State(g, pu, O.CUBIC, O.GALERKIN, I.make_f0(wl))
+        e0 = st.moments()["energy"]
+        st.run(int(round(1.0 / dt)))
+        assert st.lost[0] < 1e-30
+        out.append(abs(st.moments()["energy"] - e0))
+    return out
+
+
+@pytest.mark.parametrize("sigma2", [0.0, 0.3])
+def test_fel_rk4_is_fourth_order_and_dkd_second(sigma2):
+    """<p> + |A|^2 is invariant under the FEL equations (also with space charge: the i sigma2 |b|^2
+    term is imaginary). The Galerkin update carries the mean of p exactly, so its drift is the
+    integrator's: halving dt cuts it ~16x for RK4 (Sec. IV.B's integrator) and ~4x for DKD."""
+    rk = _energy_drifts(I.PUSH_FEL_RK4, (0.2, 0.1, 0.05), sigma2)
+    dkd = _energy_drifts(I.PUSH_FEL, (0.2, 0.1, 0.05), sigma2)
+    for a, b in zip(rk, rk[1:]):
+        assert 12.0 < a / b < 20.0
+    for a, b in zip(dkd, dkd[1:]):
+        assert 3.5 < a / b < 4.5
+    assert rk[-1] < dkd[-1] / 100
+
+
+@pytest.mark.parametrize("delta,sigma2", [(0.0, 0.0), (0.3, 0.2)])
+def test_fel_rk4_growth_matches_theory(delta, sigma2):
+    """The RK4 integrator gives the same linear growth and phase velocity of A."""
+    sp = 0.05
+    g = I.Grid(32, 256, 0.0, 2 * math.pi, -0.5, 0.5)
+    pu = I.Pusher(I.PUSH_FEL_RK4, I.POT_FREE, 1.0, 1.0, 0.02, 1e-6, 0.0, delta, sigma2)
+    wl = I.Workload("t", g, pu, I.BASIS_CUBIC, I.FP64, 0, "fel_gaussian", dict(sp=sp, eps=1e-6))
+    st = O.State(g, pu, O.CUBIC, O.GALERKIN, I.make_f0(wl))
+    nst = 500
+    hist = st.run(nst, history=True)
+    tau = (np.arange(nst) + 1) * pu.dt
+    a = hist[:, 0] + 1j * hist[:, 1]
+    sel = (tau >= 5.0) & (tau <= 10.0)
+    growth = np.polyfit(tau[sel], np.log(np.abs(a[sel])), 1)[0]
+    turn = np.polyfit(tau[sel], np.unwrap(np.angle(a[sel])), 1)[0]
+    lam = _fel_root(sp, delta, sigma2, lam=_cold_root(delta, sigma2))
+    assert abs(growth - lam.real) < 5e-3 * lam.real
+    assert abs(turn - lam.imag) < 5e-3 * max(1.0, abs(lam.imag))
+
+
 def test_fel_energy_invariant_drift_is_second_order():
     """<p> + |A|^2 is conserved by the FEL equations; DKD drift falls ~4x when dt halves."""
     drift = []
