@@ -55,7 +55,10 @@ enum {
 enum {
     VP_PUSH_LEAPFROG_KDK = 0,    /* kick-drift-kick, H = p^2/2 + V(x) */
     VP_PUSH_EXACT_ROTATION = 1,  /* linear oscillator advanced analytically (Sec. IV.A) */
-    VP_PUSH_FEL_DKD = 2          /* 1-D FEL, drift-kick-drift with A^{n+1/2} (Sec. IV.B) */
+    VP_PUSH_FEL_DKD = 2,         /* 1-D FEL, drift-kick-drift with A^{n+1/2} (Sec. IV.B) */
+    VP_PUSH_FEL_RK4 = 3          /* 1-D FEL, classical RK4 with the bunching of every stage
+                                    (the integrator of Sec. IV.B); runs on the scatter kernel,
+                                    not in batches or the server */
 };
 
 enum {

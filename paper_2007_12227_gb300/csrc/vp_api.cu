@@ -41,6 +41,7 @@ struct Plan {
     // state_s: the stored state is s = Lambda_x^{-1} r instead of the weights w
     int G, Gp, ws, threads;
     bool full_row, state_s;
+    bool rk4;   // FEL with the RK4 integrator: the scatter kernel and stage reductions
     Layout L;
 };
 
@@ -71,7 +72,7 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
         return fail(msg, VP_ERR_ARG, "grid ranges must be finite with x1 > x0 and p1 > p0");
     if (basis != VP_BASIS_TENT && basis != VP_BASIS_CUBIC_BSPLINE)
         return fail(msg, VP_ERR_ARG, "unknown basis %d", basis);
-    if (pu->kind < 0 || pu->kind > 2) return fail(msg, VP_ERR_ARG, "unknown pusher kind %d", pu->kind);
+    if (pu->kind < 0 || pu->kind > 3) return fail(msg, VP_ERR_ARG, "unknown pusher kind %d", pu->kind);
     if (pu->potential < 0 || pu->potential > 2)
         return fail(msg, VP_ERR_ARG, "unknown potential %d", pu->potential);
     if (!finite(pu->dt) || !finite(pu->v_sign) || !finite(pu->omega) || !finite(pu->a0_re) ||
@@ -102,11 +103,13 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     g.v_sign = pu->v_sign;
     g.omega = pu->omega;
     g.dt = pu->dt;
-    g.delta = pu->kind == VP_PUSH_FEL_DKD ? pu->delta : 0.0;
-    g.sigma2 = pu->kind == VP_PUSH_FEL_DKD ? pu->sigma2 : 0.0;
+    const bool fel_kind = pu->kind == VP_PUSH_FEL_DKD || pu->kind == VP_PUSH_FEL_RK4;
+    g.delta = fel_kind ? pu->delta : 0.0;
+    g.sigma2 = fel_kind ? pu->sigma2 : 0.0;
     const double h = pu->dt;
     const bool pend = pu->kind == VP_PUSH_LEAPFROG_KDK && pu->potential == VP_POT_PENDULUM;
-    P->fel = pu->kind == VP_PUSH_FEL_DKD;
+    P->fel = fel_kind;
+    P->rk4 = pu->kind == VP_PUSH_FEL_RK4;
     if (pend || P->fel) {
         const double L = grid->x1 - grid->x0, per = L / (2.0 * M_PI);
         if (fabs(per - rint(per)) > 1e-9 * per || rint(per) < 1.0)
@@ -135,6 +138,12 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     const size_t sz = opts->precision == VP_FP64 ? 8 : 4;
     const bool wide_rotation = pu->kind == VP_PUSH_EXACT_ROTATION && fabs(pu->omega * h) >= 0.5 * M_PI;
     int kernel = opts->kernel;
+    if (P->rk4) {
+        // the RK4 end point is not of the tabulated displacement form: global-atomic deposit
+        if (kernel == VP_KERNEL_FUSED)
+            return fail(msg, VP_ERR_UNSUPPORTED, "the RK4 FEL step runs on the scatter kernel");
+        kernel = VP_KERNEL_SCATTER;
+    }
     P->G = 6;
     P->Gp = 8;
     P->full_row = false;
@@ -244,7 +253,7 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     // FP32 one-pass plans: max|s| per tile of each state buffer (the fixed-point window scale)
     L.smax = take(kernel == VP_KERNEL_FUSED && sz == 4 ? 2 * (size_t)P->ntx * P->ntp * sizeof(float) : 0);
     // FEL space charge: half-drift row factors (cos, sin) for the stored state
-    L.rtil = take(P->fel && g.sigma2 != 0.0 ? 2 * (size_t)grid->np * sizeof(double) : 0);
+    L.rtil = take(P->fel && !P->rk4 && g.sigma2 != 0.0 ? 2 * (size_t)grid->np * sizeof(double) : 0);
     // one-pass plans of a push fixed for the whole run: each tile's source rectangle
     L.tsrc = take(kernel == VP_KERNEL_FUSED && !P->fel ? (size_t)P->ntx * P->ntp * sizeof(int4) : 0);
     L.state = take(ST_NSTATE * sizeof(double));
@@ -440,7 +449,15 @@ vp_status do_steps(vp_sim *s, int n, cudaEvent_t *ev = nullptr)
             VP_CUDA(s, launch_step_tiled<T>(a, s->stream));
         } else {
             VP_CUDA(s, cudaMemsetAsync(dst, 0, N * sizeof(T), s->stream));
-            VP_CUDA(s, launch_step_scatter<T>(a, s->ptr<double>(P.L.lost), s->stream));
+            if (P.rk4) {
+                VP_CUDA(s, launch_rk4_stages<T>(static_cast<const T *>(src), P.g, s->ptr<double2>(P.L.csx),
+                                                state, part, s->stream));
+                VP_CUDA(s, launch_rk4_deposit<T>(static_cast<const T *>(src), static_cast<T *>(dst), P.g,
+                                                 s->ptr<double2>(P.L.csx), state, s->ptr<double>(P.L.lost),
+                                                 s->stream));
+            } else {
+                VP_CUDA(s, launch_step_scatter<T>(a, s->ptr<double>(P.L.lost), s->stream));
+            }
         }
         if (e) VP_CUDA(s, cudaEventRecord(e[1], s->stream));
         int nparts = 0;
@@ -471,8 +488,8 @@ vp_status do_steps(vp_sim *s, int n, cudaEvent_t *ev = nullptr)
         }
         if (P.fel) {
             VP_CUDA(s, launch_fel_finalize(part, nparts, state, s->ptr<double>(P.L.hist), P.hist_cap,
-                                           P.g.dt, 0, s->stream));
-            if (P.g.sigma2 != 0.0) {
+                                           P.g.dt, 0, s->stream, P.rk4 ? 1 : 0));
+            if (P.g.sigma2 != 0.0 && !P.rk4) {
                 const vp_status sc = fel_space_charge<T>(s, dst);
                 if (sc != VP_OK) return sc;
             }
@@ -570,8 +587,8 @@ vp_status vp_create(const vp_grid *grid, int32_t basis, const vp_pusher *pusher,
     s->stream = static_cast<cudaStream_t>(opts->stream);
     s->cur = 0;
     s->f_set = false;
-    s->a0_re = pusher->kind == VP_PUSH_FEL_DKD ? pusher->a0_re : 0.0;
-    s->a0_im = pusher->kind == VP_PUSH_FEL_DKD ? pusher->a0_im : 0.0;
+    s->a0_re = s->P.fel ? pusher->a0_re : 0.0;
+    s->a0_im = s->P.fel ? pusher->a0_im : 0.0;
 
     Geometry &g = s->P.g;
     auto cleanup = [&](vp_status code) {
@@ -648,7 +665,7 @@ vp_status vp_create(const vp_grid *grid, int32_t basis, const vp_pusher *pusher,
     // FEL space charge: cos and sin of the half drift h/2 (delta + p_j), times Lambda_p^{-1}
     // (symmetric) when the stored state is s = Lambda_p w, so that sum_j w_ij f_j = sum_j s_ij rf_j
     std::vector<double> rtil;
-    if (P.fel && g.sigma2 != 0.0) {
+    if (P.fel && !P.rk4 && g.sigma2 != 0.0) {
         rtil.resize(2 * (size_t)g.np);
         for (int j = 0; j < g.np; ++j) {
             const double ph = 0.5 * g.dt * (g.delta + g.p0 + j * g.hp);
@@ -754,7 +771,7 @@ static vp_status set_f_common(vp_sim *s, const void *src, int32_t dtype, size_t 
                                                   static_cast<float *>(s->f(0)), P.g.nx, P.g.np,
                                                   s->stream));
     }
-    if (P.fel && P.g.sigma2 != 0.0) {
+    if (P.fel && !P.rk4 && P.g.sigma2 != 0.0) {
         const vp_status sc = P.precision == VP_FP64 ? fel_space_charge<double>(s, s->f(0))
                                                     : fel_space_charge<float>(s, s->f(0));
         if (sc != VP_OK) return sc;
@@ -991,6 +1008,7 @@ vp_status vp_plan(const vp_sim *s, vp_plan_info *out)
     int n = 2;
     if (P.kernel != VP_KERNEL_FUSED && P.galerkin) n += 2;
     if (P.kernel == VP_KERNEL_SCATTER && P.fel && !P.galerkin) n += 1;
+    if (P.rk4) n += 8;   // four stage reductions, each with its amplitude update
     out->launches_per_step = n;
     out->workspace_bytes = (int64_t)P.L.total;
     const bool f64 = P.precision == VP_FP64;

@@ -46,7 +46,9 @@ enum {
     ST_A_RE = 0, ST_A_IM, ST_B_RE, ST_B_IM, ST_AH_RE, ST_AH_IM, ST_TAU, ST_STEP,
     ST_M, ST_PHI,   // |K| and atan2(Re K, -Im K): amplitude and phase of the sine term
     ST_K_RE, ST_K_IM,   // FEL kick amplitude K = A^{n+1/2} + i sigma2 <exp(-i theta~)>
-    ST_NSTATE = 16
+    ST_RK_K = 16,       // RK4: K_1..K_4 (re, im), 8 slots
+    ST_RK_B = 24,       // RK4: stage bunchings b_1..b_4 (re, im), 8 slots
+    ST_NSTATE = 32
 };
 
 // Device error flag bits.
@@ -193,8 +195,18 @@ cudaError_t launch_fel_tilde(const T *state, int nx, int np, const double2 *csx,
                              const double *rs, const double *sig, double *part, cudaStream_t s);
 cudaError_t launch_fel_kick(const double *part, int nparts, double *state, double sigma2,
                             cudaStream_t s);
+// FEL RK4: the four stage reductions and amplitudes (part: rk4_stage_blocks x 3 doubles), and
+// the deposit at the RK4 end points into a zeroed destination
+int rk4_stage_blocks(int nx, int np);
+template <typename T>
+cudaError_t launch_rk4_stages(const T *w, const Geometry &g, const double2 *csx, double *state,
+                              double *part, cudaStream_t s);
+template <typename T>
+cudaError_t launch_rk4_deposit(const T *src, T *dst, const Geometry &g, const double2 *csx,
+                               const double *state, double *lost_acc, cudaStream_t s);
+// init: first bunching after vp_set_f; rk4: A^{n+1} is the RK4 value left in ST_AH
 cudaError_t launch_fel_finalize(const double *part, int nparts, double *state, double *hist,
-                                int hist_cap, double dt, int init, cudaStream_t s);
+                                int hist_cap, double dt, int init, cudaStream_t s, int rk4 = 0);
 cudaError_t launch_count_step(double *state, double dt, cudaStream_t s);
 
 template <typename T>

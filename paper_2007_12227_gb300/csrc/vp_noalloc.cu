@@ -173,7 +173,7 @@ extern "C" vp_status vp_moments_static(const void *w, int32_t dtype, const vp_gr
     out->cov_xp = m[5] / S - out->mean_x * out->mean_p;
     out->a_re = a_re_im ? a_re_im[0] : 0.0;
     out->a_im = a_re_im ? a_re_im[1] : 0.0;
-    out->energy = pusher->kind == VP_PUSH_FEL_DKD
+    out->energy = (pusher->kind == VP_PUSH_FEL_DKD || pusher->kind == VP_PUSH_FEL_RK4)
                       ? out->mean_p + out->a_re * out->a_re + out->a_im * out->a_im
                       : m[6] / S;
     out->trapped = m[7] * hh;

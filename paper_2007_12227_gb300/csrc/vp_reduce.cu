@@ -132,7 +132,7 @@ __global__ void fel_kick_kernel(const double *__restrict__ part, int nparts, dou
 
 // FEL field update from per-block partial sums (run by one block)
 __device__ void fel_finalize_block(const double *__restrict__ part, int nparts, double *state,
-                                   double *hist, int hist_cap, double dt, int init)
+                                   double *hist, int hist_cap, double dt, int init, int rk4 = 0)
 {
     __shared__ double s[3][kRedThreads];
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
@@ -166,8 +166,9 @@ __device__ void fel_finalize_block(const double *__restrict__ part, int nparts, 
         state[ST_PHI] = atan2(state[ST_AH_RE], -state[ST_AH_IM]);
         return;
     }
-    const double are = state[ST_AH_RE] + 0.5 * dt * b_re;
-    const double aim = state[ST_AH_IM] + 0.5 * dt * b_im;
+    // DKD: A^{n+1} = A^{n+1/2} + h/2 b^{n+1}; RK4: the stages left A^{n+1} in ST_AH
+    const double are = rk4 ? state[ST_AH_RE] : state[ST_AH_RE] + 0.5 * dt * b_re;
+    const double aim = rk4 ? state[ST_AH_IM] : state[ST_AH_IM] + 0.5 * dt * b_im;
     state[ST_A_RE] = are;
     state[ST_A_IM] = aim;
     state[ST_AH_RE] = are + 0.5 * dt * b_re;
@@ -188,9 +189,9 @@ __device__ void fel_finalize_block(const double *__restrict__ part, int nparts, 
 }
 
 __global__ void fel_finalize_kernel(const double *__restrict__ part, int nparts, double *state,
-                                    double *hist, int hist_cap, double dt, int init)
+                                    double *hist, int hist_cap, double dt, int init, int rk4)
 {
-    fel_finalize_block(part, nparts, state, hist, hist_cap, dt, init);
+    fel_finalize_block(part, nparts, state, hist, hist_cap, dt, init, rk4);
 }
 
 // end of a batched step: block k finishes instance k and flips its buffer parity
@@ -339,9 +340,9 @@ cudaError_t launch_fel_partials(const T *w, int nx, int np, const double2 *csx, 
 }
 
 cudaError_t launch_fel_finalize(const double *part, int nparts, double *state, double *hist,
-                                int hist_cap, double dt, int init, cudaStream_t s)
+                                int hist_cap, double dt, int init, cudaStream_t s, int rk4)
 {
-    fel_finalize_kernel<<<1, kRedThreads, 0, s>>>(part, nparts, state, hist, hist_cap, dt, init);
+    fel_finalize_kernel<<<1, kRedThreads, 0, s>>>(part, nparts, state, hist, hist_cap, dt, init, rk4);
     return cudaGetLastError();
 }
 

@@ -249,8 +249,10 @@ vp_status vp_server_submit(vp_server *s, const vp_request *req)
         (req->f0_dtype != VP_FP32 && req->f0_dtype != VP_FP64))
         return sfail(s, VP_ERR_ARG, "request %llu: bad weights, dtype or step count",
                      (unsigned long long)req->id);
-    if (req->pusher.kind == VP_PUSH_FEL_DKD && req->pusher.sigma2 != 0.0)
-        return sfail(s, VP_ERR_UNSUPPORTED, "request %llu: FEL space charge is not served in batches",
+    if ((req->pusher.kind == VP_PUSH_FEL_DKD && req->pusher.sigma2 != 0.0) ||
+        req->pusher.kind == VP_PUSH_FEL_RK4)
+        return sfail(s, VP_ERR_UNSUPPORTED,
+                     "request %llu: FEL space charge and the RK4 integrator are not served in batches",
                      (unsigned long long)req->id);
     Req *q = new (std::nothrow) Req();
     if (!q) return VP_ERR_ARG;
