@@ -23,18 +23,25 @@ _GL_X, _GL_W = np.polynomial.legendre.leggauss(4)
 
 
 def basis_value(kind: str, t: np.ndarray) -> np.ndarray:
-    """Unit-spacing basis: 'box' = top-hat of width 1, 'tent' = hat of half-width 1."""
+    """Unit-spacing basis: 'box' = top-hat of width 1, 'tent' = hat of half-width 1,
+    'cubic' = the cubic B-spline (pieces (4 - 6 t^2 + 3 |t|^3)/6 on |t| < 1, (2 - |t|)^3/6 on
+    1 <= |t| < 2)."""
     t = np.abs(t)
     if kind == "box":
         return np.where(t < 0.5, 1.0, np.where(t == 0.5, 0.5, 0.0))
     if kind == "tent":
         return np.where(t < 1.0, 1.0 - t, 0.0)
+    if kind == "cubic":
+        return np.where(t < 1.0, (4.0 - 6.0 * t ** 2 + 3.0 * t ** 3) / 6.0,
+                        np.where(t < 2.0, (2.0 - t) ** 3 / 6.0, 0.0))
     raise ValueError(kind)
 
 
 def _breaks(kind: str, c: float):
     if kind == "box":
         return [c - 0.5, c + 0.5]
+    if kind == "cubic":
+        return [c - 2.0, c - 1.0, c, c + 1.0, c + 2.0]
     return [c - 1.0, c, c + 1.0]
 
 

@@ -26,7 +26,7 @@ _lib = None
 
 KDK, ROTATION, FEL, FEL_RK4 = 0, 1, 2, 3
 FREE, PENDULUM, HARMONIC = 0, 1, 2
-TENT, CUBIC = 0, 1
+TENT, CUBIC, SEPTIC = 0, 1, 2
 GALERKIN, LUMPED = 0, 1
 
 MOMENT_NAMES = ["sum_w", "mass", "mean_x", "mean_p", "var_x", "var_p", "cov_xp",

@@ -55,7 +55,7 @@ typedef struct {
 
 enum { OR_KDK = 0, OR_ROT = 1, OR_FEL = 2, OR_FEL_RK4 = 3 };
 enum { OR_FREE = 0, OR_PEND = 1, OR_HARM = 2 };
-enum { OR_TENT = 0, OR_CUBIC = 1 };
+enum { OR_TENT = 0, OR_CUBIC = 1, OR_SEPTIC = 2 };
 enum { OR_GALERKIN = 0, OR_LUMPED = 1 };
 
 #define OR_NMOM 14
@@ -179,6 +179,32 @@ static double k_b3(double d)
     return 0.0;
 }
 
+/*
+ * Autoconvolution of the unit cubic B-spline: the septic B-spline B7 (Sec. III with cubic
+ * B-spline basis functions), from its truncated-power definition
+ *   B7(x) = 1/7! sum_{k=0..8} (-1)^k C(8, k) (x + 4 - k)_+^7,
+ * evaluated at -|x| (even function), where at most four terms are nonzero.
+ */
+static double k_b7(double d)
+{
+    const double x = -fabs(d);
+    if (x <= -4.0) return 0.0;
+    static const double c8[9] = {1, 8, 28, 56, 70, 56, 28, 8, 1};
+    double s = 0.0;
+    for (int k = 0; k <= 8; ++k) {
+        const double t = x + 4.0 - k;
+        if (t <= 0.0) break;
+        const double t7 = t * t * t * t * t * t * t;
+        s += (k & 1 ? -c8[k] : c8[k]) * t7;
+    }
+    return s / 5040.0;
+}
+
+static double k_basis(int basis, double d)
+{
+    return basis == OR_TENT ? k_tent(d) : (basis == OR_CUBIC ? k_b3(d) : k_b7(d));
+}
+
 static long mod_l(long a, long n)
 {
     long r = a % n;
@@ -256,6 +282,85 @@ void or_mass_solve(const or_grid *g, double *r)
         for (int j = 0; j < np; ++j) r[(long)j * nx + i] = col[j];
     }
     free(work);
+}
+
+/*
+ * Galerkin mass-matrix solve for cubic B-spline basis functions: Lambda = Lambda_x (x) Lambda_p
+ * with the 7-band Toeplitz matrix h B7(j - k) per axis (B7 at 0, 1, 2, 3 = 2416, 1191, 120, 1
+ * over 5040). Along x (periodic) the matrix is circulant: solved exactly by its eigenvalues
+ * lambda_k = h sum_d B7(d) cos(2 pi d k / nx) with a direct DFT. Along p the basis is not
+ * truncated and the matrix is the np x np principal block: banded Gaussian elimination
+ * (symmetric positive definite, no pivoting).
+ */
+void or_mass_solve7(const or_grid *g, double *r)
+{
+    const int nx = g->nx, np = g->np;
+    const double hx = grid_hx(g), hp = grid_hp(g);
+    double b[4];
+    for (int d = 0; d < 4; ++d) b[d] = k_b7((double)d);
+    /* x: circulant */
+    double *cs = (double *)malloc(sizeof(double) * 5 * nx);
+    double *sn = cs + nx, *lam = sn + nx, *re = lam + nx, *im = re + nx;
+    for (int m = 0; m < nx; ++m) {
+        const double twopi = 6.283185307179586476925286766559;
+        cs[m] = cos(twopi * m / nx);
+        sn[m] = sin(twopi * m / nx);
+    }
+    for (int k = 0; k < nx; ++k) {
+        double l = b[0];
+        for (int d = 1; d < 4; ++d) l += 2.0 * b[d] * cs[(long)d * k % nx];
+        lam[k] = hx * l;
+    }
+    for (int j = 0; j < np; ++j) {
+        double *row = r + (long)j * nx;
+        for (int k = 0; k < nx; ++k) {
+            double sr = 0.0, si = 0.0;
+            for (int i = 0; i < nx; ++i) {
+                const long m = (long)i * k % nx;
+                sr += row[i] * cs[m];
+                si -= row[i] * sn[m];
+            }
+            re[k] = sr / lam[k];
+            im[k] = si / lam[k];
+        }
+        for (int i = 0; i < nx; ++i) {
+            double s = 0.0;
+            for (int k = 0; k < nx; ++k) {
+                const long m = (long)i * k % nx;
+                s += re[k] * cs[m] - im[k] * sn[m];
+            }
+            row[i] = s / nx;
+        }
+    }
+    free(cs);
+    /* p: banded elimination of the principal block (half-bandwidth 3) */
+    double *a = (double *)malloc(sizeof(double) * 7 * (size_t)np);   /* a[j*7 + 3 + o]: (j, j+o) */
+    double *col = (double *)malloc(sizeof(double) * (size_t)np);
+    for (int i = 0; i < nx; ++i) {
+        for (int j = 0; j < np; ++j) {
+            for (int o = -3; o <= 3; ++o)
+                a[(size_t)j * 7 + 3 + o] = (j + o >= 0 && j + o < np) ? hp * b[o < 0 ? -o : o] : 0.0;
+            col[j] = r[(long)j * nx + i];
+        }
+        for (int k = 0; k < np; ++k) {
+            const double piv = a[(size_t)k * 7 + 3];
+            for (int j = k + 1; j <= k + 3 && j < np; ++j) {
+                const double f = a[(size_t)j * 7 + 3 + (k - j)] / piv;
+                if (f == 0.0) continue;
+                for (int o = 0; o <= 3 && k + o < np; ++o)
+                    a[(size_t)j * 7 + 3 + (k + o - j)] -= f * a[(size_t)k * 7 + 3 + o];
+                col[j] -= f * col[k];
+            }
+        }
+        for (int k = np - 1; k >= 0; --k) {
+            double s = col[k];
+            for (int o = 1; o <= 3 && k + o < np; ++o) s -= a[(size_t)k * 7 + 3 + o] * col[k + o];
+            col[k] = s / a[(size_t)k * 7 + 3];
+        }
+        for (int j = 0; j < np; ++j) r[(long)j * nx + i] = col[j];
+    }
+    free(col);
+    free(a);
 }
 
 /* ------------------------------------------------------------------ step */
@@ -336,7 +441,7 @@ int or_step(const or_grid *g, int basis, int projection, const or_pusher *pu,
         a_new_re = fel[0] + h / 6.0 * (b[0] + 2.0 * b[2] + 2.0 * b[4] + b[6]);
         a_new_im = fel[1] + h / 6.0 * (b[1] + 2.0 * b[3] + 2.0 * b[5] + b[7]);
     }
-    const double radius = (basis == OR_TENT) ? 1.0 : 2.0;
+    const double radius = (basis == OR_TENT) ? 1.0 : (basis == OR_CUBIC ? 2.0 : 4.0);
     double lost_acc = 0.0;
     memset(w_out, 0, sizeof(double) * n);
 
@@ -357,10 +462,10 @@ int or_step(const or_grid *g, int basis, int projection, const or_pusher *pu,
             const long c_lo = (long)ceil(u - radius), c_hi = (long)floor(u + radius);
             const long r_lo = (long)ceil(v - radius), r_hi = (long)floor(v + radius);
             for (long rr = r_lo; rr <= r_hi; ++rr) {
-                const double kp = hp * (basis == OR_TENT ? k_tent(rr - v) : k_b3(rr - v));
+                const double kp = hp * k_basis(basis, rr - v);
                 if (kp == 0.0) continue;
                 for (long cc = c_lo; cc <= c_hi; ++cc) {
-                    const double kx = hx * (basis == OR_TENT ? k_tent(cc - u) : k_b3(cc - u));
+                    const double kx = hx * k_basis(basis, cc - u);
                     const double contrib = kx * kp * w;
                     if (rr < 0 || rr >= np) {
                         lost_acc += contrib;
@@ -374,6 +479,8 @@ int or_step(const or_grid *g, int basis, int projection, const or_pusher *pu,
     /* Lambda w_fin = r */
     if (basis == OR_CUBIC && projection == OR_GALERKIN) {
         or_mass_solve(g, w_out);
+    } else if (basis == OR_SEPTIC && projection == OR_GALERKIN) {
+        or_mass_solve7(g, w_out);
     } else {
         const double inv = 1.0 / (hx * hp);
         for (long k = 0; k < n; ++k) w_out[k] *= inv;

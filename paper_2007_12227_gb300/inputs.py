@@ -19,7 +19,8 @@ from typing import List, Optional
 import numpy as np
 
 # enum values mirror include/vlasov.h
-BASIS_TENT, BASIS_CUBIC = 0, 1
+# deposit kernels: tent (top-hat basis), B3 (tent basis), B7 (cubic B-spline basis)
+BASIS_TENT, BASIS_CUBIC, BASIS_SEPTIC = 0, 1, 2
 PUSH_KDK, PUSH_ROTATION, PUSH_FEL, PUSH_FEL_RK4 = 0, 1, 2, 3
 POT_FREE, POT_PENDULUM, POT_HARMONIC = 0, 1, 2
 FP32, FP64 = 0, 1

@@ -33,7 +33,8 @@ def _pushed_cells(g, pu, a=(0.0, 0.0)):
 @pytest.mark.parametrize("shape", [(8, 8), (9, 7)])
 @pytest.mark.parametrize("pusher", ["pendulum", "rotation", "fel"])
 @pytest.mark.parametrize("basis,proj", [(O.TENT, O.GALERKIN), (O.CUBIC, O.GALERKIN),
-                                        (O.CUBIC, O.LUMPED)])
+                                        (O.CUBIC, O.LUMPED), (O.SEPTIC, O.GALERKIN),
+                                        (O.SEPTIC, O.LUMPED)])
 def test_step_equals_dense_integral_definition(shape, pusher, basis, proj):
     """Sec. III: w_fin = Lambda^{-1} Delta^T w_in with Lambda, Delta as integrals."""
     nx, np_ = shape
@@ -56,7 +57,7 @@ def test_step_equals_dense_integral_definition(shape, pusher, basis, proj):
         a = (fel[0] + 0.5 * h * fel[2], fel[1] + 0.5 * h * fel[3])
     w = rng.random((np_, nx)) - 0.2
     u, v = _pushed_cells(g, pu, a)
-    kind = "box" if basis == O.TENT else "tent"
+    kind = {O.TENT: "box", O.CUBIC: "tent", O.SEPTIC: "cubic"}[basis]
     want = B.dense_step(nx, np_, g.hx, g.hp, kind, u, v, w, lumped=(proj == O.LUMPED))
     got, _, _ = O.step(g, basis, proj, pu, w, fel)
     assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
@@ -564,3 +565,47 @@ def test_paper_pendulum_negative_weights_galerkin_only():
     assert gal.moments()["neg_mass"] < -1e-6
     assert tent.moments()["neg_mass"] == 0.0
     assert abs(gal.moments()["mass"] + gal.lost[0] * g.hx * g.hp - 1.0) < 5e-3
+
+
+# ------------------------------------------------- smoother basis (Sec. V remark), measured
+def test_cubic_spline_basis_galerkin_has_more_negative_weight_than_tent_basis():
+    """Sec. V suggests smoother basis functions might ameliorate the negative weights. With the
+    Galerkin (L2) projection onto cubic B-spline basis functions (B7 deposit, 7-band Lambda) the
+    negative mass of the paper's flat-top FEL and pendulum runs is larger than with the tent
+    basis, not smaller; the lumped projection (non-negative deposit) keeps every weight >= 0."""
+    hw = PAPER["fel_flattop_half_width"]["value"]
+    g = I.Grid(64, 128, 0.0, 2 * math.pi, -0.5, 0.5)
+    pu = I.Pusher(I.PUSH_FEL, I.POT_FREE, 1.0, 1.0, 0.05, 1e-2, 0.0)
+    wl = I.Workload("t", g, pu, I.BASIS_CUBIC, I.FP64, 0, "fel_flattop", dict(half_width=hw, eps=1e-2))
+    neg = {}
+    for basis in (O.CUBIC, O.SEPTIC):
+        st = O.State(g, pu, basis, O.GALERKIN, I.make_f0(wl))
+        st.run(5)
+        neg[basis] = st.moments()["neg_mass"]
+    assert neg[O.SEPTIC] < 1.2 * neg[O.CUBIC] < 0.0
+    st = O.State(g, pu, O.SEPTIC, O.LUMPED, I.make_f0(wl))
+    st.run(5)
+    assert st.moments()["neg_mass"] == 0.0
+
+
+def test_septic_galerkin_transports_mean_and_covariance_under_rotation():
+    """The cubic B-spline basis Galerkin step also carries the mean and covariance of a
+    Gaussian exactly through a rigid rotation (as the tent basis does)."""
+    omega = 1.0
+    g = I.Grid(96, 96, -9.0, 9.0, -9.0, 9.0)
+    pu = I.Pusher(I.PUSH_ROTATION, I.POT_HARMONIC, 1.0, omega, math.pi / 10)
+    X, P = np.meshgrid(g.x_nodes(), g.p_nodes())
+    f0 = np.exp(-0.5 * ((X - 0.8) / 0.5) ** 2 - 0.5 * ((P + 0.3) / 0.9) ** 2 - 0.4 * (X - 0.8) * (P + 0.3))
+    st = O.State(g, pu, O.SEPTIC, O.GALERKIN, f0)
+    m0 = st.moments()
+    nst = 3
+    st.run(nst)
+    m1 = st.moments()
+    th = omega * pu.dt * nst
+    R = np.array([[math.cos(th), math.sin(th) / omega], [-omega * math.sin(th), math.cos(th)]])
+    mu0 = np.array([m0["mean_x"], m0["mean_p"]])
+    S0 = np.array([[m0["var_x"], m0["cov_xp"]], [m0["cov_xp"], m0["var_p"]]])
+    mu1 = np.array([m1["mean_x"], m1["mean_p"]])
+    S1 = np.array([[m1["var_x"], m1["cov_xp"]], [m1["cov_xp"], m1["var_p"]]])
+    assert np.max(np.abs(mu1 - R @ mu0)) < 1e-12
+    assert np.max(np.abs(S1 - R @ S0 @ R.T)) < 1e-11
