@@ -48,7 +48,9 @@ typedef enum vp_status {
 /* Deposition kernel = autoconvolution of the basis (Sec. III, Delta). */
 enum {
     VP_BASIS_TENT = 0,           /* top-hat basis: tent deposit, Lambda = h I (orthogonal) */
-    VP_BASIS_CUBIC_BSPLINE = 1   /* tent basis: cubic B-spline deposit, Lambda = h tridiag(1/6,2/3,1/6) */
+    VP_BASIS_CUBIC_BSPLINE = 1,  /* tent basis: cubic B-spline deposit, Lambda = h tridiag(1/6,2/3,1/6) */
+    VP_BASIS_SEPTIC_BSPLINE = 2  /* cubic B-spline basis (smoother basis, Sec. V): septic B-spline
+                                    deposit, Lambda = h B7(j - k), 7 bands; scatter kernel */
 };
 
 /* Particle pusher for the node flow (Sec. II; examples of Sec. IV). */

@@ -28,7 +28,7 @@ constexpr int kMoutLen = 32;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-    size_t f0, f1, tmp, col, row, rowb, vcb, rowbf, vcbf, csx, ucol, vcol, piv, sigma, smax, tsrc, rtil,
+    size_t f0, f1, tmp, col, row, rowb, vcb, rowbf, vcbf, csx, ucol, vcol, piv, ldl, sigma, smax, tsrc, rtil,
         state, hist,
         lost, part, mpart, mout, err, total;
 };
@@ -42,6 +42,8 @@ struct Plan {
     int G, Gp, ws, threads;
     bool full_row, state_s;
     bool rk4;   // FEL with the RK4 integrator: the scatter kernel and stage reductions
+    bool septic_gal;   // cubic B-spline basis, Galerkin: 7-band solves after the scatter deposit
+    double x7_scale;   // septic x solve: the scale that gives the recursions a unit DC gain
     Layout L;
 };
 
@@ -70,7 +72,7 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     if (!finite(grid->x0) || !finite(grid->x1) || !finite(grid->p0) || !finite(grid->p1) ||
         !(grid->x1 > grid->x0) || !(grid->p1 > grid->p0))
         return fail(msg, VP_ERR_ARG, "grid ranges must be finite with x1 > x0 and p1 > p0");
-    if (basis != VP_BASIS_TENT && basis != VP_BASIS_CUBIC_BSPLINE)
+    if (basis != VP_BASIS_TENT && basis != VP_BASIS_CUBIC_BSPLINE && basis != VP_BASIS_SEPTIC_BSPLINE)
         return fail(msg, VP_ERR_ARG, "unknown basis %d", basis);
     if (pu->kind < 0 || pu->kind > 3) return fail(msg, VP_ERR_ARG, "unknown pusher kind %d", pu->kind);
     if (pu->potential < 0 || pu->potential > 2)
@@ -135,13 +137,16 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     P->precision = opts->precision;
     P->projection = opts->projection;
     P->galerkin = basis == VP_BASIS_CUBIC_BSPLINE && opts->projection == VP_PROJ_GALERKIN;
+    P->septic_gal = basis == VP_BASIS_SEPTIC_BSPLINE && opts->projection == VP_PROJ_GALERKIN;
     const size_t sz = opts->precision == VP_FP64 ? 8 : 4;
     const bool wide_rotation = pu->kind == VP_PUSH_EXACT_ROTATION && fabs(pu->omega * h) >= 0.5 * M_PI;
     int kernel = opts->kernel;
-    if (P->rk4) {
-        // the RK4 end point is not of the tabulated displacement form: global-atomic deposit
+    if (P->rk4 || basis == VP_BASIS_SEPTIC_BSPLINE) {
+        // the RK4 end point is not of the tabulated displacement form, and the 8-tap septic
+        // deposit has no one-pass form here: global-atomic deposit
         if (kernel == VP_KERNEL_FUSED)
-            return fail(msg, VP_ERR_UNSUPPORTED, "the RK4 FEL step runs on the scatter kernel");
+            return fail(msg, VP_ERR_UNSUPPORTED,
+                        "the RK4 FEL step and the septic deposit run on the scatter kernel");
         kernel = VP_KERNEL_SCATTER;
     }
     P->G = 6;
@@ -208,7 +213,7 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
             return fail(msg, VP_ERR_UNSUPPORTED, "tile %d x %d needs %zu bytes of shared memory", tx,
                         tp, smem);
     }
-    if (P->galerkin) {
+    if (P->galerkin || P->septic_gal) {
         const size_t smem = (size_t)(grid->nx + grid->nx / 32 + 1) * sz;
         if (smem > kMaxSmem)
             return fail(msg, VP_ERR_UNSUPPORTED,
@@ -238,7 +243,7 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     };
     L.f0 = take(N * sz);
     L.f1 = take(N * sz);
-    L.tmp = take(P->galerkin ? N * sz : 0);
+    L.tmp = take(P->galerkin || P->septic_gal ? N * sz : 0);
     L.col = take(grid->nx * colsz);
     L.row = take(grid->np * rowsz);
     L.rowb = take(grid->np * sizeof(RowBound));
@@ -249,6 +254,7 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     L.ucol = take(grid->nx * sizeof(double));
     L.vcol = take(grid->nx * sizeof(double));
     L.piv = take(kPivTable * sizeof(double));
+    L.ldl = take(P->septic_gal ? (size_t)(kLdlRows + 1) * 4 * sizeof(double) : 0);
     L.sigma = take(grid->np * sizeof(double));
     // FP32 one-pass plans: max|s| per tile of each state buffer (the fixed-point window scale)
     L.smax = take(kernel == VP_KERNEL_FUSED && sz == 4 ? 2 * (size_t)P->ntx * P->ntp * sizeof(float) : 0);
@@ -473,6 +479,20 @@ vp_status do_steps(vp_sim *s, int n, cudaEvent_t *ev = nullptr)
                                           P.fel ? 1 : 0, err, s->stream));
             if (e) VP_CUDA(s, cudaEventRecord(e[3], s->stream));
             nparts = filter_p_blocks(P.g.nx, P.g.np);
+        } else if (P.septic_gal) {
+            T *tmp = s->ptr<T>(P.L.tmp);
+            const double sh = P.precision == VP_FP32 ? (double)(float)P.x7_scale : P.x7_scale;
+            VP_CUDA(s, launch_filter_x7<T>(static_cast<const T *>(dst), tmp, P.g.nx, P.g.np, sh,
+                                           P.x7_scale - sh, s->stream));
+            if (e) VP_CUDA(s, cudaEventRecord(e[2], s->stream));
+            VP_CUDA(s, launch_filter_p7<T>(tmp, static_cast<T *>(dst), P.g.nx, P.g.np, s->ptr<double>(P.L.ldl),
+                                           s->stream));
+            if (e) VP_CUDA(s, cudaEventRecord(e[3], s->stream));
+            if (P.fel) {
+                VP_CUDA(s, launch_fel_partials<T>(static_cast<const T *>(dst), P.g.nx, P.g.np,
+                                                  s->ptr<double2>(P.L.csx), part, s->stream));
+                nparts = fel_partial_blocks(P.g.nx, P.g.np);
+            }
         } else if (P.fel) {
             if (P.kernel == VP_KERNEL_TILED) {
                 nparts = P.ntx * P.ntp;
@@ -482,7 +502,7 @@ vp_status do_steps(vp_sim *s, int n, cudaEvent_t *ev = nullptr)
                 nparts = fel_partial_blocks(P.g.nx, P.g.np);
             }
         }
-        if (e && (!P.galerkin || P.kernel == VP_KERNEL_FUSED)) {
+        if (e && ((!P.galerkin && !P.septic_gal) || P.kernel == VP_KERNEL_FUSED)) {
             VP_CUDA(s, cudaEventRecord(e[2], s->stream));
             VP_CUDA(s, cudaEventRecord(e[3], s->stream));
         }
@@ -633,6 +653,32 @@ vp_status vp_create(const vp_grid *grid, int32_t basis, const vp_pusher *pusher,
         vcb[2 * b + 1] = hi;
     }
     // Thomas pivots of tridiag(1/6, 2/3, 1/6) from the first row, and their limits
+    // septic basis: LDL^T factor rows of the principal block of P7 (exact for the first kLdlRows
+    // rows, then the limit), and the x scale prod (1 - z_i)^2 with the poles as the kernel holds
+    // them, which makes the recursions' DC gain one
+    std::vector<double> ldl;
+    if (P.septic_gal) {
+        const double bb[4] = {2416.0 / 5040.0, 1191.0 / 5040.0, 120.0 / 5040.0, 1.0 / 5040.0};
+        ldl.assign((size_t)(kLdlRows + 1) * 4, 0.0);
+        auto D = [&](int r) -> double & { return ldl[(size_t)r * 4]; };
+        auto Lm = [&](int r, int m) -> double & { return ldl[(size_t)r * 4 + m]; };   // L_{r+m, r}
+        for (int jr = 0; jr <= kLdlRows; ++jr) {
+            double d = bb[0];
+            for (int k = 1; k <= 3 && jr - k >= 0; ++k) d -= Lm(jr - k, k) * Lm(jr - k, k) * D(jr - k);
+            D(jr) = d;
+            for (int m = 1; m <= 3; ++m) {
+                double v = bb[m];
+                for (int k = 1; k + m <= 3 && jr - k >= 0; ++k) v -= Lm(jr - k, m + k) * Lm(jr - k, k) * D(jr - k);
+                Lm(jr, m) = v / d;
+            }
+        }
+        double sc = 1.0;
+        for (int q = 0; q < 3; ++q) {
+            const double zq = P.precision == VP_FP32 ? (double)(float)septic_pole(q) : septic_pole(q);
+            sc *= (1.0 - zq) * (1.0 - zq);
+        }
+        s->P.x7_scale = sc;
+    }
     std::vector<double> piv(kPivTable, 0.0);
     double cprev = 0.0;
     for (int r = 0; r < kPivots; ++r) {
@@ -702,6 +748,12 @@ vp_status vp_create(const vp_grid *grid, int32_t basis, const vp_pusher *pusher,
                             cudaMemcpyHostToDevice, s->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
         if (e != cudaSuccess) return cleanup(cuda_fail(nullptr, e, "space-charge table upload"));
+    }
+    if (!ldl.empty()) {
+        e = cudaMemcpyAsync(s->ws + P.L.ldl, ldl.data(), ldl.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, s->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s->stream);
+        if (e != cudaSuccess) return cleanup(cuda_fail(nullptr, e, "septic factor upload"));
     }
     e = cudaMemcpyAsync(s->ws + P.L.sigma, sigma.data(), sigma.size() * sizeof(double),
                         cudaMemcpyHostToDevice, s->stream);
@@ -1006,7 +1058,8 @@ vp_status vp_plan(const vp_sim *s, vp_plan_info *out)
     out->state_is_s = P.state_s ? 1 : 0;
     // step kernel (+ filters along x and p) (+ FEL partials) + field update or step counter
     int n = 2;
-    if (P.kernel != VP_KERNEL_FUSED && P.galerkin) n += 2;
+    if (P.kernel != VP_KERNEL_FUSED && (P.galerkin || P.septic_gal)) n += 2;
+    if (P.septic_gal && P.fel) n += 1;   // FEL partial sums after the septic solves
     if (P.kernel == VP_KERNEL_SCATTER && P.fel && !P.galerkin) n += 1;
     if (P.rk4) n += 8;   // four stage reductions, each with its amplitude update
     out->launches_per_step = n;

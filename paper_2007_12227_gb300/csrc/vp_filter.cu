@@ -206,6 +206,147 @@ cudaError_t launch_filter_x(const T *in, T *out, int nx, int np, const double *p
     return cudaGetLastError();
 }
 
+// ---- septic B-spline Galerkin solves (cubic B-spline basis functions) ------------------
+namespace {
+
+
+// Along x (periodic): P7^{-1} = gain prod_i 1 / ((1 - z_i q)(1 - z_i / q)), one causal and one
+// anticausal first-order recursion per pole over the row held in shared memory. Each thread
+// sweeps its chunk; its start value is the geometric sum of the preceding (following) elements
+// over one period, truncated at |z|^K below the rounding of T, times 1 / (1 - z^nx).
+template <typename T>
+__global__ void filter_x7_kernel(const T *__restrict__ in, T *__restrict__ out, int nx, int np, T sh, T sl)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *buf = reinterpret_cast<T *>(smem_raw);
+    const int j = blockIdx.x;
+    const T *src = in + (size_t)j * nx;
+    T *dst = out + (size_t)j * nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) buf[padx(i)] = src[i];
+    __syncthreads();
+    const int C = (nx + blockDim.x - 1) / blockDim.x;
+    const int s = threadIdx.x * C;
+    const int e = min(s + C, nx);
+    const bool active = s < nx;
+    const double eps = sizeof(T) == 4 ? 1e-9 : 1e-18;
+    for (int q = 0; q < 3; ++q) {
+        const double zd = septic_pole(q);
+        const T z = (T)zd;
+        int K = (int)ceil(log(eps) / log(fabs(zd)));
+        if (K > nx) K = nx;
+        const T cyc = (T)(1.0 / (1.0 - pow(zd, (double)nx)));
+        T init = T(0);
+        if (active) {   // causal: y_{s-1}
+            T zk = T(1);
+            int idx = s - 1;
+            if (idx < 0) idx += nx;
+            for (int k = 0; k < K; ++k) {
+                init += zk * buf[padx(idx)];
+                zk *= z;
+                if (--idx < 0) idx += nx;
+            }
+            init *= cyc;
+        }
+        __syncthreads();
+        if (active) {
+            T y = init;
+            for (int i = s; i < e; ++i) {
+                y = buf[padx(i)] + z * y;
+                buf[padx(i)] = y;
+            }
+        }
+        __syncthreads();
+        if (active) {   // anticausal: u_e
+            T zk = T(1);
+            int idx = e;
+            if (idx >= nx) idx -= nx;
+            init = T(0);
+            for (int k = 0; k < K; ++k) {
+                init += zk * buf[padx(idx)];
+                zk *= z;
+                if (++idx >= nx) idx -= nx;
+            }
+            init *= cyc;
+        }
+        __syncthreads();
+        if (active) {
+            T u = init;
+            for (int i = e - 1; i >= s; --i) {
+                u = buf[padx(i)] + z * u;
+                buf[padx(i)] = u;
+            }
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const T v = buf[padx(i)];
+        dst[i] = v * sh + v * sl;
+    }
+}
+
+// Along p (open): the np x np principal block of P7 = L D L^T, L unit lower with three
+// subdiagonals; the factor rows are exact up to kLdlRows and their limit beyond
+// (ldl[4 r] = D_r, ldl[4 r + m] = L_{r+m, r}). One thread per column: forward and back
+// substitution.
+template <typename T>
+__global__ void filter_p7_kernel(const T *__restrict__ in, T *__restrict__ out, int nx, int np,
+                                 const double *__restrict__ ldl)
+{
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= nx) return;
+    auto row = [&](int r) { return ldl + 4 * (size_t)(r < kLdlRows ? r : kLdlRows); };
+    T y1 = T(0), y2 = T(0), y3 = T(0);   // y_{j-1}, y_{j-2}, y_{j-3}
+    for (int j = 0; j < np; ++j) {
+        T y = in[(size_t)j * nx + col];
+        if (j >= 1) y -= (T)row(j - 1)[1] * y1;
+        if (j >= 2) y -= (T)row(j - 2)[2] * y2;
+        if (j >= 3) y -= (T)row(j - 3)[3] * y3;
+        y3 = y2;
+        y2 = y1;
+        y1 = y;
+        out[(size_t)j * nx + col] = y / (T)row(j)[0];
+    }
+    T w1 = T(0), w2 = T(0), w3 = T(0);   // w_{j+1}, w_{j+2}, w_{j+3}
+    for (int j = np - 1; j >= 0; --j) {
+        const double *rj = row(j);
+        T w = out[(size_t)j * nx + col];
+        if (j + 1 < np) w -= (T)rj[1] * w1;
+        if (j + 2 < np) w -= (T)rj[2] * w2;
+        if (j + 3 < np) w -= (T)rj[3] * w3;
+        w3 = w2;
+        w2 = w1;
+        w1 = w;
+        out[(size_t)j * nx + col] = w;
+    }
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_filter_x7(const T *in, T *out, int nx, int np, double sh, double sl, cudaStream_t s)
+{
+    const size_t smem = (size_t)(nx + nx / 32 + 1) * sizeof(T);
+    cudaError_t e = cudaFuncSetAttribute(filter_x7_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    filter_x7_kernel<T><<<np, 256, smem, s>>>(in, out, nx, np, (T)sh, (T)sl);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_filter_p7(const T *in, T *out, int nx, int np, const double *ldl, cudaStream_t s)
+{
+    filter_p7_kernel<T><<<(nx + 127) / 128, 128, 0, s>>>(in, out, nx, np, ldl);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_filter_x7<float>(const float *, float *, int, int, double, double, cudaStream_t);
+template cudaError_t launch_filter_x7<double>(const double *, double *, int, int, double, double,
+                                              cudaStream_t);
+template cudaError_t launch_filter_p7<float>(const float *, float *, int, int, const double *, cudaStream_t);
+template cudaError_t launch_filter_p7<double>(const double *, double *, int, int, const double *,
+                                              cudaStream_t);
+
 int filter_p_blocks(int nx, int np)
 {
     const int W = kPCols * kPWarps;

@@ -127,6 +127,42 @@ struct FusedArgs {
 };
 constexpr int kTileSrcUnset = (int)0x80808080;   // the bytes 0x80 (cudaMemset)
 
+// Tap weights of the septic B-spline B7 (the deposit kernel of cubic B-spline basis
+// functions) for a node at fraction t in [0, 1) past cell m: w[a] = B7(t + 3 - a) for the
+// cells m - 3 .. m + 4, by the Cox-de Boor recursion of the cardinal B-splines
+// M_d(x) = (x M_{d-1}(x) + (d + 1 - x) M_{d-1}(x - 1)) / d, M_0 = 1 on [0, 1):
+// v[k] = M_d(t + k), k = 0..d, and B7(y) = M_7(y + 4).
+template <typename T>
+__device__ __forceinline__ void septic_weights(T t, T *w)
+{
+    T v[8];
+    v[0] = T(1);
+#pragma unroll
+    for (int d = 1; d <= 7; ++d) {
+        T nv[8];
+#pragma unroll
+        for (int k = 0; k <= d; ++k) {
+            const T a = k < d ? v[k] : T(0);
+            const T b = k > 0 ? v[k - 1] : T(0);
+            nv[k] = ((t + T(k)) * a + (T(d + 1) - t - T(k)) * b) / T(d);
+        }
+#pragma unroll
+        for (int k = 0; k <= d; ++k) v[k] = nv[k];
+    }
+#pragma unroll
+    for (int a = 0; a < 8; ++a) w[a] = v[7 - a];
+}
+
+// The septic B-spline mass matrix 1/5040 (1, 120, 1191, 2416, 1191, 120, 1) factors as
+// gain * prod_i 1 / ((1 - z_i q)(1 - z_i / q)) with these poles (roots inside the unit circle
+// of q^6 + 120 q^5 + 1191 q^4 + 2416 q^3 + 1191 q^2 + 120 q + 1), gain = 5040 prod (-z_i).
+constexpr double septic_pole(int q)
+{
+    return q == 0 ? -0.53528043079643816554 : (q == 1 ? -0.12255461519232669052 : -0.0091486948096082769286);
+}
+// Lambda_p LDL^T factor rows kept exactly (then their limit): D_j and L_{j+m, j}, m = 1..3
+constexpr int kLdlRows = 96;
+
 // ---- launch entry points (defined in the .cu files) -----------------------
 cudaError_t build_tables(const Geometry &g, int precision, void *col, void *row,
                          RowBound *rowb, double *ucol, double *vcol, double2 *csx, cudaStream_t s);
@@ -170,6 +206,13 @@ cudaError_t launch_tile_max(const float *s, float *map, int nx, int np, int tx, 
 template <typename T>
 cudaError_t launch_filter_x(const T *in, T *out, int nx, int np, const double *piv, unsigned *err,
                             cudaStream_t s);
+// septic B-spline Galerkin solves: cyclic 3-pole recursion along x (scale: float pair
+// sh + sl), LDL^T of the np x np principal block along p (ldl: (kLdlRows + 1) rows of D, L1..L3)
+template <typename T>
+cudaError_t launch_filter_x7(const T *in, T *out, int nx, int np, double sh, double sl,
+                             cudaStream_t s);
+template <typename T>
+cudaError_t launch_filter_p7(const T *in, T *out, int nx, int np, const double *ldl, cudaStream_t s);
 template <typename T>
 cudaError_t launch_filter_p(const T *in, T *out, int nx, int np, const double *piv,
                             const double2 *csx, double *part, int want_part, unsigned *err,

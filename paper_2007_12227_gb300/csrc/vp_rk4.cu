@@ -141,6 +141,11 @@ struct RkTaps<T, VP_BASIS_TENT> {
     }
 };
 template <typename T>
+struct RkTaps<T, VP_BASIS_SEPTIC_BSPLINE> {
+    static constexpr int N = 8, LO = -3;
+    __device__ static void weights(T t, T *w) { septic_weights<T>(t, w); }
+};
+template <typename T>
 struct RkTaps<T, VP_BASIS_CUBIC_BSPLINE> {
     static constexpr int N = 4, LO = -1;
     __device__ static void weights(T t, T *w)
@@ -237,6 +242,9 @@ cudaError_t launch_rk4_deposit(const T *src, T *dst, const Geometry &g, const do
     if (grid > 152 * 32) grid = 152 * 32;
     if (g.basis == VP_BASIS_TENT)
         rk4_deposit_kernel<T, VP_BASIS_TENT><<<grid, kThreads, 0, s>>>(src, dst, g, csx, state, lost_acc);
+    else if (g.basis == VP_BASIS_SEPTIC_BSPLINE)
+        rk4_deposit_kernel<T, VP_BASIS_SEPTIC_BSPLINE><<<grid, kThreads, 0, s>>>(src, dst, g, csx, state,
+                                                                                lost_acc);
     else
         rk4_deposit_kernel<T, VP_BASIS_CUBIC_BSPLINE><<<grid, kThreads, 0, s>>>(src, dst, g, csx, state,
                                                                                lost_acc);

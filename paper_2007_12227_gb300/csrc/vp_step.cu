@@ -46,6 +46,13 @@ struct Taps<T, VP_BASIS_TENT> {
 };
 
 template <typename T>
+struct Taps<T, VP_BASIS_SEPTIC_BSPLINE> {
+    static constexpr int N = 8;
+    static constexpr int LO = -3;
+    __device__ __forceinline__ static void weights(T t, T *w) { septic_weights<T>(t, w); }
+};
+
+template <typename T>
 struct Taps<T, VP_BASIS_CUBIC_BSPLINE> {
     static constexpr int N = 4;
     static constexpr int LO = -1;
@@ -400,6 +407,8 @@ cudaError_t launch_step_scatter(const StepArgs<T> &a, double *lost_acc, cudaStre
     if (grid > 152 * 64) grid = 152 * 64;
     if (a.g.basis == VP_BASIS_TENT)
         step_scatter_kernel<T, VP_BASIS_TENT><<<grid, kThreads, 0, s>>>(a, lost_acc);
+    else if (a.g.basis == VP_BASIS_SEPTIC_BSPLINE)
+        step_scatter_kernel<T, VP_BASIS_SEPTIC_BSPLINE><<<grid, kThreads, 0, s>>>(a, lost_acc);
     else
         step_scatter_kernel<T, VP_BASIS_CUBIC_BSPLINE><<<grid, kThreads, 0, s>>>(a, lost_acc);
     return cudaGetLastError();

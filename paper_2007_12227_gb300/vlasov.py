@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libvlasov.so")
 
 VP_OK, VP_ERR_ARG, VP_ERR_CUDA, VP_ERR_WORKSPACE, VP_ERR_NONFINITE, VP_ERR_TIMEOUT, \
     VP_ERR_STATE, VP_ERR_UNSUPPORTED = range(8)
-VP_BASIS_TENT, VP_BASIS_CUBIC_BSPLINE = 0, 1
+VP_BASIS_TENT, VP_BASIS_CUBIC_BSPLINE, VP_BASIS_SEPTIC_BSPLINE = 0, 1, 2
 VP_PUSH_LEAPFROG_KDK, VP_PUSH_EXACT_ROTATION, VP_PUSH_FEL_DKD, VP_PUSH_FEL_RK4 = 0, 1, 2, 3
 VP_POT_FREE, VP_POT_PENDULUM, VP_POT_HARMONIC = 0, 1, 2
 VP_FP32, VP_FP64 = 0, 1
