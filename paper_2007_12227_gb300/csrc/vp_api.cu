@@ -393,14 +393,14 @@ FusedArgs<T> fused_args(vp_sim *s, const void *src, void *dst)
 
 // the weights w of the current state: the state itself, or Lambda_p^{-1} s in scratch
 template <typename T>
-vp_status weights_of_state(vp_sim *s, const void **w)
+vp_status weights_of_state(vp_sim *s, const void **w, void *out = nullptr)
 {
     const Plan &P = s->P;
     if (!P.state_s) {
         *w = s->f(s->cur);
         return VP_OK;
     }
-    T *tmp = s->ptr<T>(P.L.tmp);
+    T *tmp = out ? static_cast<T *>(out) : s->ptr<T>(P.L.tmp);
     VP_CUDA(s, launch_filter_p<T>(static_cast<const T *>(s->f(s->cur)), tmp, P.g.nx, P.g.np,
                                   s->ptr<double>(P.L.piv), s->ptr<double2>(P.L.csx),
                                   s->ptr<double>(P.L.part), 0, s->ptr<unsigned>(P.L.err), s->stream));
@@ -774,6 +774,21 @@ vp_status vp_create(const vp_grid *grid, int32_t basis, const vp_pusher *pusher,
     return VP_OK;
 }
 
+// Device address of a host buffer that kernels can read and write in place (pinned or
+// registered host memory; on Grace-Blackwell the chip-to-chip link is coherent), else nullptr.
+// Transfers through it run at the link's rate like a copy, and fuse the copy with the solve
+// that precedes or follows it.
+static void *host_device_ptr(const void *p, size_t align)
+{
+    if ((uintptr_t)p % align) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 static vp_status set_f_common(vp_sim *s, const void *src, int32_t dtype, size_t n, bool device)
 {
     if (!s) return VP_ERR_ARG;
@@ -785,7 +800,11 @@ static vp_status set_f_common(vp_sim *s, const void *src, int32_t dtype, size_t 
     // the weights go to the state buffer, or to scratch when the state is s = Lambda_p w
     void *dst = P.state_s ? (void *)(s->ws + P.L.tmp) : s->f(0);
     const size_t szs = P.precision == VP_FP64 ? 8 : 4;
-    if (dtype == P.precision) {
+    // pinned host weights and the state s = Lambda_p w: Lambda_p reads them in place
+    void *hdev = (!device && dtype == P.precision && P.state_s) ? host_device_ptr(src, szs) : nullptr;
+    if (hdev) {
+        dst = hdev;
+    } else if (dtype == P.precision) {
         VP_CUDA(s, cudaMemcpyAsync(dst, src, N * szs,
                                    device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                                    s->stream));
@@ -832,6 +851,8 @@ static vp_status set_f_common(vp_sim *s, const void *src, int32_t dtype, size_t 
         VP_CUDA(s, launch_tile_max(static_cast<const float *>(s->f(0)), s->ptr<float>(P.L.smax), P.g.nx,
                                    P.g.np, P.tx, P.tp, P.ntx, P.ntp, s->ptr<unsigned>(P.L.err),
                                    s->stream));
+    // the caller owns the host buffer again once set_f returns
+    if (hdev) VP_CUDA(s, cudaStreamSynchronize(s->stream));
     return VP_OK;
 }
 
@@ -899,13 +920,17 @@ static vp_status get_f_common(vp_sim *s, void *dstp, int32_t dtype, size_t n, bo
         return fail(s->msg, VP_ERR_ARG, "get_f: need room for %zu values of dtype FP32/FP64", N);
     if (!s->f_set) return fail(s->msg, VP_ERR_STATE, "vp_get_f before vp_set_f");
     const void *src = nullptr;
+    const size_t szs = P.precision == VP_FP64 ? 8 : 4;
+    // a pinned host buffer and the state s = Lambda_p w: the p solve writes the weights in place
+    void *hdev = (!device && dtype == P.precision && P.state_s) ? host_device_ptr(dstp, szs) : nullptr;
     {
-        vp_status st = P.precision == VP_FP64 ? weights_of_state<double>(s, &src)
-                                              : weights_of_state<float>(s, &src);
+        vp_status st = P.precision == VP_FP64 ? weights_of_state<double>(s, &src, hdev)
+                                              : weights_of_state<float>(s, &src, hdev);
         if (st != VP_OK) return st;
     }
-    const size_t szs = P.precision == VP_FP64 ? 8 : 4;
-    if (dtype == P.precision) {
+    if (hdev) {
+        // the p solve above wrote the weights into the host buffer
+    } else if (dtype == P.precision) {
         VP_CUDA(s, cudaMemcpyAsync(dstp, src, N * szs,
                                    device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                                    s->stream));

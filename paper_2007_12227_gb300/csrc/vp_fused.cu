@@ -1176,18 +1176,27 @@ cudaError_t launch_step_fused(const FusedArgs<T> &a, int threads, cudaStream_t s
     return cudaGetLastError();
 }
 
-// s = Lambda_p w along columns (tridiag(1/6, 2/3, 1/6), zero beyond the open edges)
+// s = Lambda_p w along columns (tridiag(1/6, 2/3, 1/6), zero beyond the open edges). Each thread
+// walks one column through a chunk of kMulRows rows, so every input row is read once (plus a halo
+// row at either end of the chunk): w may be host memory the device reads in place.
+constexpr int kMulRows = 64;
+constexpr int kMulCols = 256;
+
 template <typename T>
-__global__ void lambda_p_mul_kernel(const T *__restrict__ w, T *__restrict__ s, int nx, int np)
+__global__ void __launch_bounds__(kMulCols)
+    lambda_p_mul_kernel(const T *__restrict__ w, T *__restrict__ s, int nx, int np)
 {
-    const size_t n = (size_t)nx * np;
-    for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
-         idx += (size_t)gridDim.x * blockDim.x) {
-        const int j = (int)(idx / nx);
-        const T c = w[idx];
-        const T lo = j > 0 ? w[idx - nx] : T(0);
-        const T hi = j + 1 < np ? w[idx + nx] : T(0);
-        s[idx] = (lo + hi) * (T(1) / T(6)) + c * (T(2) / T(3));
+    const int col = blockIdx.x * kMulCols + threadIdx.x;
+    if (col >= nx) return;
+    const int j0 = blockIdx.y * kMulRows, j1 = min(j0 + kMulRows, np);
+    T lo = j0 > 0 ? w[(size_t)(j0 - 1) * nx + col] : T(0);
+    T c = w[(size_t)j0 * nx + col];
+#pragma unroll 8
+    for (int j = j0; j < j1; ++j) {
+        const T hi = j + 1 < np ? w[(size_t)(j + 1) * nx + col] : T(0);
+        s[(size_t)j * nx + col] = (lo + hi) * (T(1) / T(6)) + c * (T(2) / T(3));
+        lo = c;
+        c = hi;
     }
 }
 
@@ -1229,9 +1238,9 @@ cudaError_t launch_tile_max(const float *s, float *map, int nx, int np, int tx, 
 template <typename T>
 cudaError_t launch_lambda_p_mul(const T *w, T *s, int nx, int np, cudaStream_t st)
 {
-    size_t b = ((size_t)nx * np + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
-    lambda_p_mul_kernel<T><<<(int)b, 256, 0, st>>>(w, s, nx, np);
+    const dim3 grid((nx + kMulCols - 1) / kMulCols, (np + kMulRows - 1) / kMulRows);
+    if (grid.y > 65535u) return cudaErrorInvalidConfiguration;
+    lambda_p_mul_kernel<T><<<grid, kMulCols, 0, st>>>(w, s, nx, np);
     return cudaGetLastError();
 }
 
