@@ -149,7 +149,7 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
                         "the RK4 FEL step and the septic deposit run on the scatter kernel");
         kernel = VP_KERNEL_SCATTER;
     }
-    P->G = 6;
+    P->G = 8;   // a multiple of 4, so that the x solve's rows start 16-byte aligned
     P->Gp = 8;
     P->full_row = false;
     P->ws = 0;
@@ -169,7 +169,9 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
         if (!full && ftx + 2 * halo > kFusedMaxRow) ftx = kFusedMaxRow - 2 * halo;
         ftp = std::min(std::min(ftp, grid->np), kFusedMaxTileP);
         const int WW = full ? grid->nx + 2 * G : ftx + 2 * halo + 2 * G;
-        const int ws = (WW + 31) / 32 * 32 + 1;
+        // row stride a multiple of 32 words: the rows start 16-byte aligned, and lanes that
+        // deposit into adjacent columns of two neighbouring rows hit distinct banks
+        const int ws = (WW + 31) / 32 * 32;
         const int wsrc = (full ? grid->nx : ftx + 2 * halo) + 2 * R + 8;
         // two CTAs per SM (up to 320 threads) unless the tile is wide: then one CTA of up
         // to 576 threads per SM

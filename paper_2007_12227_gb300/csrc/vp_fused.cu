@@ -26,7 +26,8 @@
 // Contributions outside the window belong to other tiles, except rows beyond
 // the open momentum edge, which are counted as lost by the tile owning the
 // column. Finally each warp takes window rows, solves Lambda_x along them
-// (first-order recurrences combined across lanes with a warp scan), and the
+// (first-order recurrences over per-lane chunks, combined across lanes by a warp
+// scan, or on windowed rows by the carries of the neighbouring chunks), and the
 // tile is stored once.
 #include <math.h>
 
@@ -590,15 +591,21 @@ constexpr double zconst(int n)
 
 // Lambda_x^{-1} of one window row of exactly 32 KX elements (the common case of the
 // windowed tiles): the recurrences start from zero at both row ends and every power of z
-// the lane sweeps and the warp scans need is a compile-time constant.
+// the lane sweeps and the carries need is a compile-time constant. row == nullptr: v
+// already holds the lane's KX elements.
+// A lane's carry is the recurrence value at the end of the chunks next to it. Where the
+// halo spans at most three chunks it sums only those chunks' zero-start end values (two
+// or three shuffles, no scan): what it leaves out is weighted by |z|^halo or less, the
+// truncation the recurrences already have at the window ends.
 template <typename T, int KX>
 __device__ __forceinline__ void solve_row_x_exact(const T *row, int lane, T *v, bool padded, T sh,
                                                   T sl)
 {
     const int base = lane * KX;
     const T z = (T)zconst(1);
+    if (row)
 #pragma unroll
-    for (int k = 0; k < KX; ++k) v[k] = row[padded ? padc(base + k) : base + k];
+        for (int k = 0; k < KX; ++k) v[k] = row[padded ? padc(base + k) : base + k];
     // causal y_i = x_i + z y_{i-1}: lane-local, then the carry of the lanes below
     T y = T(0);
 #pragma unroll
@@ -607,13 +614,23 @@ __device__ __forceinline__ void solve_row_x_exact(const T *row, int lane, T *v, 
         v[k] = y;
     }
     T endv = y;
+    T carry = T(0);
+    constexpr int NCH = (Halo<T>::value + KX - 1) / KX;
+    if constexpr (NCH <= 3) {
 #pragma unroll
-    for (int s = 0; s < 5; ++s) {
-        const T o = __shfl_up_sync(0xffffffffu, endv, 1 << s);
-        if (lane >= (1 << s)) endv += (T)zconst(KX << s) * o;
+        for (int c = 1; c <= NCH; ++c) {
+            const T o = __shfl_up_sync(0xffffffffu, endv, c);
+            if (lane >= c) carry += (T)zconst((c - 1) * KX) * o;
+        }
+    } else {
+#pragma unroll
+        for (int s = 0; s < 5; ++s) {
+            const T o = __shfl_up_sync(0xffffffffu, endv, 1 << s);
+            if (lane >= (1 << s)) endv += (T)zconst(KX << s) * o;
+        }
+        carry = __shfl_up_sync(0xffffffffu, endv, 1);
+        if (lane == 0) carry = T(0);
     }
-    T carry = __shfl_up_sync(0xffffffffu, endv, 1);
-    if (lane == 0) carry = T(0);
 #pragma unroll
     for (int k = 0; k < KX; ++k) v[k] += (T)zconst(k + 1) * carry;
     // anticausal u_i = y_i + z u_{i+1}
@@ -624,13 +641,22 @@ __device__ __forceinline__ void solve_row_x_exact(const T *row, int lane, T *v, 
         v[k] = u;
     }
     T startv = u;
+    T carry2 = T(0);
+    if constexpr (NCH <= 3) {
 #pragma unroll
-    for (int s = 0; s < 5; ++s) {
-        const T o = __shfl_down_sync(0xffffffffu, startv, 1 << s);
-        if (lane + (1 << s) < 32) startv += (T)zconst(KX << s) * o;
+        for (int c = 1; c <= NCH; ++c) {
+            const T o = __shfl_down_sync(0xffffffffu, startv, c);
+            if (lane + c < 32) carry2 += (T)zconst((c - 1) * KX) * o;
+        }
+    } else {
+#pragma unroll
+        for (int s = 0; s < 5; ++s) {
+            const T o = __shfl_down_sync(0xffffffffu, startv, 1 << s);
+            if (lane + (1 << s) < 32) startv += (T)zconst(KX << s) * o;
+        }
+        carry2 = __shfl_down_sync(0xffffffffu, startv, 1);
+        if (lane == 31) carry2 = T(0);
     }
-    T carry2 = __shfl_down_sync(0xffffffffu, startv, 1);
-    if (lane == 31) carry2 = T(0);
 #pragma unroll
     for (int k = 0; k < KX; ++k) v[k] += (T)zconst(KX - k) * carry2;
 #pragma unroll
@@ -656,15 +682,30 @@ __device__ __forceinline__ void gal_rows(T *win, const WinGeom &W, T *dst, int L
         T v[KX];
         int per, base;
         const bool exact = !full && L == 32 * KX;
-        // window cells to weight units: into the staging copy, else in place
-        if (use_stage) {
+        // FP32 rows of 32 KX cells starting 16-byte aligned: each lane reads its chunk of
+        // fixed-point cells with vector loads, without a staging copy
+        const bool direct = sizeof(T) == 4 && exact && KX % 4 == 0 &&
+                            ((reinterpret_cast<uintptr_t>(row) & 15) == 0);
+        if (direct) {
+            const int4 *r4 = reinterpret_cast<const int4 *>(row + lane * KX);
+#pragma unroll
+            for (int k4 = 0; k4 < KX / 4; ++k4) {
+                const int4 q = r4[k4];
+                v[4 * k4 + 0] = (T)q.x * iq;
+                v[4 * k4 + 1] = (T)q.y * iq;
+                v[4 * k4 + 2] = (T)q.z * iq;
+                v[4 * k4 + 3] = (T)q.w * iq;
+            }
+        } else if (use_stage) {
+            // window cells to weight units: into the staging copy, else in place
             for (int c = lane; c < L; c += 32) stage[padc(c)] = wget(row + c, iq);
         } else if (sizeof(T) == 4) {
             for (int c = lane; c < L; c += 32) row[c] = wget(row + c, iq);
         }
         __syncwarp();
         if (exact) {
-            solve_row_x_exact<T, KX>(use_stage ? stage : row, lane, v, use_stage, sh, sl);
+            solve_row_x_exact<T, KX>(direct ? nullptr : (use_stage ? stage : row), lane, v,
+                                     use_stage && !direct, sh, sl);
             per = KX;
             base = lane * KX;
         } else {
@@ -693,7 +734,8 @@ __device__ __forceinline__ void gal_rows(T *win, const WinGeom &W, T *dst, int L
             if (want_part)
 #pragma unroll
                 for (int k = 0; k < KX; ++k) row[base + k] = v[k];   // keep s for the column sums
-        } else {
+        } else if (!(exact && (base + KX <= D || base >= D + TXe))) {
+            // (lanes whose chunk lies in the halo store nothing)
 #pragma unroll
             for (int k = 0; k < KX; ++k) {
                 const int c = base + k;
