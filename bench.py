@@ -91,8 +91,9 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def traffic_from_profile(kernel_file, source_files):
-    """Per-launch DRAM bytes from the committed ncu summary, if the kernel is unchanged."""
+def traffic_from_profile(kernel_file, source_files, tile=None):
+    """Per-launch DRAM bytes from the committed ncu summary, if the kernel is unchanged and the
+    summary was taken with the same tile shape."""
     path = os.path.join(ROOT, "profiles", kernel_file)
     if not os.path.exists(path):
         return None
@@ -105,6 +106,9 @@ def traffic_from_profile(kernel_file, source_files):
     for sf in source_files:
         digest.update(open(os.path.join(ROOT, sf), "rb").read())
     if digest.hexdigest() != h.group(1):
+        return None
+    t = re.search(r"^tile:\s*(\d+)x(\d+)", text, re.M)
+    if tile is not None and (not t or (int(t.group(1)), int(t.group(2))) != tuple(tile)):
         return None
     return float(m.group(1))
 
@@ -357,6 +361,7 @@ def main():
     # kernels per vp_step on this plan: the one-pass step kernel and the step counter
     # (FEL: the field update); the separate-filter plan adds the two Lambda solves
     launches_per_step = 2 if sim.kernel() == V.VP_KERNEL_FUSED else 4
+    plan = sim.plan()
 
     # ---- per-phase device time (same stream, events between the kernels)
     nprof = min(args.steps, 500)
@@ -376,7 +381,9 @@ def main():
                                      ["paper_2007_12227_gb300/csrc/vp_filter.cu"])}
     traffic = None
     if names[dom] in kernel_files:
-        traffic = traffic_from_profile(*kernel_files[names[dom]])
+        traffic = traffic_from_profile(*kernel_files[names[dom]],
+                                       tile=(plan["tile_x"], plan["tile_p"]) if names[dom] == "push_deposit"
+                                       else None)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": names[dom],
                 "peak_source": f"{peak_kind} hbm_gbs",
@@ -447,7 +454,7 @@ def main():
                 "dtype": "f32", "data": "synthetic",
                 "config": {"workload": wl.name, "mesh": f"{g.nx}x{g.np}", "dt": wl.pusher.dt,
                            "basis": "cubic_bspline_galerkin", "parallelism": f"replicas{ws}",
-                           "tile": [tuned["tile_x"], tuned["tile_p"]],
+                           "tile": [plan["tile_x"], plan["tile_p"]],
                            "autotune": {"seconds": t_tune, "candidates": tuned["candidates"],
                                         "tuned_ms_per_step": tuned["ms_per_step"],
                                         "default_ms_per_step": tuned["default_ms_per_step"]},

@@ -40,11 +40,14 @@ std::vector<Shape> candidate_shapes(int precision, bool batched)
 {
     std::vector<Shape> c{{0, 0}};
     static const int w32[] = {96, 128, 160, 192, 224, 256, 320, 384, 448};
-    static const int h32[] = {16, 32, 64, 128};
+    // heights include multiples of the warp counts of the common widths (60 = 6 x 10, 63 = 9 x 7),
+    // which give each warp of the x solve the same number of window rows; which height wins
+    // depends mostly on how the tile count fills the waves of 2 CTAs per SM, so it is measured
+    static const int h32[] = {16, 32, 60, 63, 64, 128};
     static const int w64[] = {64, 96, 128, 192, 256};
     static const int h64[] = {16, 32, 64};
     static const int wb[] = {128, 160, 224, 320};
-    static const int hb[] = {16, 32, 64};
+    static const int hb[] = {16, 32, 63, 64};
     if (batched) {
         for (int w : wb)
             for (int h : hb) c.push_back({w, h});
