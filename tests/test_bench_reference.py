@@ -1,0 +1,31 @@
+"""The bench's reference arm: the serial FP64 oracle timed on the host cores.
+
+Runs `bench.py --impl reference` for one step of each workload (on its reduced sample mesh) and
+checks the JSON line the benchmark contract asks for. No GPU is needed.
+"""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.mark.parametrize("workload,full", [("pendulum", "pendulum_8192x8192_fp32_cubic"),
+                                           ("fel", "fel_4096x2048_fp32_cubic")])
+def test_reference_arm_line(workload, full):
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", workload,
+                          "--steps", "1", "--warmup", "3"],
+                         cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference"
+    assert line["unit"] == "node-updates/s" and line["higher_is_better"] is True
+    assert line["value"] > 0 and line["steps"] == 1 and line["warmup"] == 3
+    assert line["config"]["workload"] == full
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
