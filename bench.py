@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-serve", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=40)
+    ap.add_argument("--serve-count", type=int, default=60,
+                    help="requests of the serving trace to run (the whole fixed trace is 2000)")
     ap.add_argument("--tile", default="", help="TX,TP: fixed tile shape instead of the autotuner's")
     return ap.parse_args()
 
@@ -282,7 +284,8 @@ def bench_serve(V, torch, stream, count=60, budget_gb=150.0, rate=500.0):
     srv.close()
     lat = sorted(done[r.rid]["t_finish"] - (t0 + r.arrival) for r in reqs)
     work = sum(r.workload.grid.nodes * r.workload.steps for r in reqs)
-    return {"requests": count, "trace": f"Poisson {rate:.3g}/s, seed 2007122272 (prefix)",
+    part = "full" if count >= 2000 else "prefix"
+    return {"requests": count, "trace": f"Poisson {rate:.3g}/s, seed 2007122272 ({part})",
             "rate_per_s": rate, "offered_node_updates_per_s": rate * work / count,
             "node_updates": work, "wall_s": wall, "node_updates_per_s": work / wall,
             "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
@@ -497,12 +500,13 @@ def main():
     if not args.skip_extra and rank == 0 and not args.skip_batch:
         extra["batch_256"] = bench_batch(V, torch, stream, args.batch_steps)
     if not args.skip_extra and rank == 0 and not args.skip_serve:
-        extra["served"] = bench_serve(V, torch, stream)
+        extra["served"] = bench_serve(V, torch, stream, count=args.serve_count)
         # the same requests at ~70% of the batched throughput: a queue that stays bounded
         cap = extra.get("batch_256", {}).get("batched_node_updates_per_s", 4e10)
-        reqs = I.serving_trace(count=60)
+        reqs = I.serving_trace(count=args.serve_count)
         mean_work = sum(r.workload.grid.nodes * r.workload.steps for r in reqs) / len(reqs)
-        extra["served_rho0.7"] = bench_serve(V, torch, stream, rate=0.7 * cap / mean_work)
+        extra["served_rho0.7"] = bench_serve(V, torch, stream, count=args.serve_count,
+                                             rate=0.7 * cap / mean_work)
 
     cpu = None
     if rank == 0 and not args.skip_cpu:
