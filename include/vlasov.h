@@ -149,8 +149,12 @@ vp_status vp_create(const vp_grid *grid, int32_t basis, const vp_pusher *pusher,
                     const vp_opts *opts, void *workspace, size_t workspace_bytes, vp_sim **out);
 
 /* Set the weights from host memory ([np][nx], dtype VP_FP32 / VP_FP64, n = nx*np).
- * Converts to the sim's precision; pinned host memory makes the copy asynchronous
- * when dtype equals the sim precision. Resets step, tau, lost mass and A = A0. */
+ * Converts to the sim's precision. Returns once the weights have been read: the
+ * caller owns the buffer again. When the stored state is s = Lambda_p w (fused
+ * Galerkin plan), dtype equals the sim precision and the buffer is pinned or
+ * registered host memory aligned to dtype, the Lambda_p multiply reads it in place
+ * (no staging copy); otherwise it is copied to the device first.
+ * Resets step, tau, lost mass and A = A0. */
 vp_status vp_set_f(vp_sim *sim, const void *host, int32_t dtype, size_t n);
 /* Same from device memory (device-to-device on the sim's stream). */
 vp_status vp_set_f_device(vp_sim *sim, const void *dev, int32_t dtype, size_t n);
@@ -167,7 +171,10 @@ vp_status vp_step(vp_sim *sim, int32_t n);
 #define VP_NPHASES 4
 vp_status vp_step_profiled(vp_sim *sim, int32_t n, double *phase_ms, int32_t nphases);
 
-/* Copy the weights out ([np][nx] in dtype). vp_get_f synchronises the stream. */
+/* Copy the weights out ([np][nx] in dtype). vp_get_f synchronises the stream. When
+ * the stored state is s = Lambda_p w, dtype equals the sim precision and the buffer
+ * is pinned or registered host memory aligned to dtype, the p solve writes the
+ * weights into it in place; otherwise they are staged on the device and copied. */
 vp_status vp_get_f(vp_sim *sim, void *host, int32_t dtype, size_t n);
 vp_status vp_get_f_device(vp_sim *sim, void *dev, int32_t dtype, size_t n);
 
