@@ -42,7 +42,8 @@ typedef enum vp_status {
     VP_ERR_NONFINITE = 4,   /* a step produced a NaN or infinity (device flag) */
     VP_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up (device flag) */
     VP_ERR_STATE = 6,       /* call out of order (e.g. vp_step before vp_set_f) */
-    VP_ERR_UNSUPPORTED = 7  /* valid request this build cannot serve (size limits) */
+    VP_ERR_UNSUPPORTED = 7, /* valid request this build cannot serve (size limits) */
+    VP_ERR_CANCELLED = 8    /* a served request was cancelled (vp_server_cancel) */
 } vp_status;
 
 /* Deposition kernel = autoconvolution of the basis (Sec. III, Delta). */
@@ -189,17 +190,21 @@ vp_status vp_field_history(vp_sim *sim, double *re_im, size_t max_entries, size_
 vp_status vp_sync(vp_sim *sim);
 
 /* Moments of a weight array the caller already holds on the device, with no
- * device allocation: for callers that cannot allocate when they need the
- * diagnostics (during CUDA-graph capture, under a framework allocator that owns
- * the device, in time-critical loops). The paper has no counterpart; it gives
- * the same FP64 reductions as vp_moments. w: device pointer, [np][nx] of dtype
- * VP_FP32 or VP_FP64; lost_mass and a_re_im (host, may be NULL) are copied into
- * the result; stream: cudaStream_t (NULL = default); synchronises that stream.
+ * device allocation. The paper has no counterpart. It serves callers that cannot
+ * allocate device memory when they want the diagnostics: an application whose
+ * framework allocator already holds the device's memory (a cudaMalloc would fail
+ * or make that allocator give its cache back), or a latency-critical loop that
+ * must not take the device synchronisation a cudaMalloc or cudaFree can bring.
+ * It gives the FP64 moments vp_moments gives (plain FP64 sums in another
+ * summation order, so the two agree to rounding). w: device pointer, [np][nx]
+ * of dtype VP_FP32 or VP_FP64; lost_mass and a_re_im (host, may be NULL) are
+ * copied into the result; stream: cudaStream_t (NULL = default); the call reads
+ * the result back to the host and synchronises that stream.
  * The partial sums live in one static device array of this library (about
  * 427 KB per GPU, held until exit); meshes above 2^26 nodes are rejected with
  * VP_ERR_UNSUPPORTED. The first call on a device looks up that array's device
- * address, so make it before any stream capture. Calls share the array:
- * calls that overlap on the GPU race. */
+ * address (kept for the process; not valid across a cudaDeviceReset). Calls
+ * share the array: calls that overlap on the GPU race. */
 vp_status vp_moments_static(const void *w, int32_t dtype, const vp_grid *grid,
                             const vp_pusher *pusher, double lost_mass, const double *a_re_im,
                             vp_moments_t *out, void *stream);
@@ -299,6 +304,16 @@ vp_status vp_server_submit(vp_server *srv, const vp_request *req);
 vp_status vp_server_run(vp_server *srv, int32_t rounds, int32_t *queued, int32_t *active);
 /* Move up to max finished results into out; *count receives how many. */
 vp_status vp_server_poll(vp_server *srv, vp_result *out, int32_t max, int32_t *count);
+/* Cancel request id (the first queued or running request with that id). A queued
+ * request leaves the queue at once; a running one is retired at the start of the
+ * next scheduling round, before any further step, and its device memory returns to
+ * the arena. Either way its result arrives through vp_server_poll with status
+ * VP_ERR_CANCELLED and the moments of its state when it was retired (a queued
+ * request has none); no final weights are kept. The other requests are not
+ * affected: each simulation's arithmetic does not depend on the batch it runs in.
+ * Returns VP_ERR_STATE if no queued or running request has that id (e.g. it has
+ * finished already). Host-side only: no device work, no wait. */
+vp_status vp_server_cancel(vp_server *srv, uint64_t id);
 /* Final weights of a finished request submitted with keep_f (then released). */
 vp_status vp_server_take_f(vp_server *srv, uint64_t id, void *host, int32_t dtype, size_t n);
 /* Host steady-clock seconds, the clock of vp_result. */

@@ -572,6 +572,7 @@ const char *vp_status_string(vp_status st)
     case VP_ERR_TIMEOUT: return "device wait timed out";
     case VP_ERR_STATE: return "call out of order";
     case VP_ERR_UNSUPPORTED: return "unsupported size or option";
+    case VP_ERR_CANCELLED: return "cancelled";
     }
     return "unknown status";
 }

@@ -1,13 +1,14 @@
 // vp_noalloc.cu -- moments of a weight array with no device allocation at all.
 //
-// Some callers cannot allocate device memory when they need the diagnostics:
-// code running while a CUDA graph is being captured (cudaMalloc is not allowed
-// then), hosts whose framework allocator already owns the whole device, or
-// time-critical loops that must not wait on an allocation. vp_moments_static
-// gives them the same FP64 moments as vp_moments for any FP32 or FP64 weight
-// array they already hold on the device: its per-block partial sums and the
-// final sums live in one file-scope device array of this library, so the
-// caller passes only the input, the mesh description and the output.
+// Some callers cannot allocate device memory at the moment they want the
+// diagnostics: a host application whose framework allocator already holds all
+// of the device's memory (a cudaMalloc would fail, or force that allocator to
+// give its cache back), or a latency-critical loop that must not take the
+// implicit device synchronisation a cudaMalloc or cudaFree can bring.
+// vp_moments_static gives them the same FP64 moments as vp_moments for an FP32
+// or FP64 weight array they already hold on the device: its per-block partial
+// sums and the final sums live in one file-scope device array of this library,
+// so the caller passes only the input, the mesh description and the output.
 //
 // The array is kMaxBlocks * kNumMoments partial sums plus the final sums
 // (about 427 KB); every GPU that loads the library holds it until the process
@@ -16,10 +17,16 @@
 // on one stream without ordering) race, and each call keeps the previous
 // call's contents until its own blocks overwrite them (every slot it reads is
 // written first in the same call, so nothing needs clearing).
+//
+// The sums are plain FP64 sums, formed per thread, then by warp shuffles and
+// in a fixed order over the warps and the blocks, as vp_moments forms its own
+// (vp_moments uses another block count, so the two differ by rounding only).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdio.h>
 #include <string.h>
+
+#include <mutex>
 
 #include "vp_internal.h"
 
@@ -33,10 +40,13 @@ constexpr int kOut = 16;                              // final sums (13 moments 
 
 static __device__ __align__(256) double g_scratch[kMaxBlocks * vp::kNumMoments + kOut];
 
-// device address of g_scratch per device, looked up once with that device current
+// device address of g_scratch per device, looked up once with that device current and kept
+// for the life of the process (a cudaDeviceReset of that device invalidates it: this entry
+// point is not meant to be used across a device reset). g_mu orders the first calls of
+// several host threads.
 constexpr int kMaxDevices = 64;
+std::mutex g_mu;
 double *g_addr[kMaxDevices];
-bool g_ready[kMaxDevices];
 
 template <typename T>
 __global__ void moments_static_kernel(const T *__restrict__ w, vp::Geometry g, double *scratch)
@@ -68,7 +78,7 @@ __global__ void moments_static_kernel(const T *__restrict__ w, vp::Geometry g, d
         acc[5] += ww * x * p;
         acc[6] += ww * H;
         if (pend && H < hsep) acc[7] += ww;
-        if (wt > T(0)) acc[8] -= (double)(wt * log(wt));
+        if (wt > T(0)) acc[8] -= ww * log(ww);   // in FP64 for FP32 weights too
         else acc[9] += ww;
         acc[10] += ww * cx;
         acc[11] += ww * sx;
@@ -122,15 +132,18 @@ extern "C" vp_status vp_moments_static(const void *w, int32_t dtype, const vp_gr
     }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return VP_ERR_CUDA;
-    if (!g_ready[dev]) {
-        // the host-side name g_scratch is not a device address: look the address up once
-        // per device, with that device current (before any stream capture)
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return VP_ERR_CUDA;
-        g_addr[dev] = static_cast<double *>(p);
-        g_ready[dev] = true;
+    double *scratch = nullptr;
+    {
+        // the host-side name g_scratch is not a device address: look the address up once per
+        // device, with that device current, and check the lookup
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_addr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return VP_ERR_CUDA;
+            g_addr[dev] = static_cast<double *>(p);
+        }
+        scratch = g_addr[dev];
     }
-    double *scratch = g_addr[dev];
     vp::Geometry g;
     memset(&g, 0, sizeof(g));
     g.nx = grid->nx;

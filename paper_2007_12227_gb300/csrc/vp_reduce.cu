@@ -216,10 +216,12 @@ __global__ void count_step_kernel(double *state, double dt)
     state[ST_TAU] = st * dt;
 }
 
+// w ln w in FP64, for FP32 weights too (the entropy is an FP64 reduction)
 template <typename T>
 __device__ __forceinline__ double wlogw(T w)
 {
-    return (double)(w * log(w));
+    const double d = (double)w;
+    return d * log(d);
 }
 
 template <typename T>

@@ -88,6 +88,7 @@ struct Req {
     int done = 0;
     double t_submit = 0, t_admit = 0, t_finish = 0;
     bool batched = false;
+    bool cancelled = false;   // retire at the start of the next round
 };
 
 }  // namespace
@@ -216,6 +217,33 @@ vp_status rebuild_batch(vp_server *s)
     return VP_OK;
 }
 
+// requests cancelled while running leave before the round steps anything
+void retire_cancelled(vp_server *s)
+{
+    std::vector<Req *> keep;
+    for (Req *q : s->active) {
+        if (!q->cancelled) {
+            keep.push_back(q);
+            continue;
+        }
+        if (s->batch) drop_batch(s);   // a member leaves: the batch is rebuilt
+        vp_result res{};
+        res.id = q->r.id;
+        res.batched = q->batched ? 1 : 0;
+        vp_status st = vp_moments(q->sim, &res.moments);
+        res.status = st == VP_OK ? VP_ERR_CANCELLED : st;
+        res.t_submit = q->t_submit;
+        res.t_admit = q->t_admit;
+        res.t_finish = q->t_finish = now_s();
+        s->finished.push_back(res);
+        vp_destroy(q->sim);
+        s->alloc.release(q->off, q->bytes);
+        delete q;
+        s->dirty = true;
+    }
+    s->active.swap(keep);
+}
+
 }  // namespace
 
 extern "C" {
@@ -269,6 +297,7 @@ vp_status vp_server_run(vp_server *s, int32_t rounds, int32_t *queued, int32_t *
 {
     if (!s) return VP_ERR_ARG;
     for (int r = 0; r < rounds; ++r) {
+        retire_cancelled(s);
         admit(s);
         if (s->active.empty()) break;
         if (s->dirty) rebuild_batch(s);
@@ -324,6 +353,31 @@ vp_status vp_server_run(vp_server *s, int32_t rounds, int32_t *queued, int32_t *
     if (queued) *queued = (int32_t)s->queue.size();
     if (active) *active = (int32_t)s->active.size();
     return VP_OK;
+}
+
+vp_status vp_server_cancel(vp_server *s, uint64_t id)
+{
+    if (!s) return VP_ERR_ARG;
+    for (auto it = s->queue.begin(); it != s->queue.end(); ++it) {
+        Req *q = *it;
+        if (q->r.id != id) continue;
+        vp_result res{};
+        res.id = id;
+        res.status = VP_ERR_CANCELLED;
+        res.t_submit = q->t_submit;
+        res.t_admit = res.t_finish = now_s();
+        s->finished.push_back(res);
+        s->queue.erase(it);
+        delete q;
+        return VP_OK;
+    }
+    for (Req *q : s->active)
+        if (q->r.id == id && !q->cancelled) {
+            q->cancelled = true;
+            return VP_OK;
+        }
+    return sfail(s, VP_ERR_STATE, "request %llu is neither queued nor running",
+                 (unsigned long long)id);
 }
 
 vp_status vp_server_poll(vp_server *s, vp_result *out, int32_t max, int32_t *count)

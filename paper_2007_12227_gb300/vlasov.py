@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libvlasov.so")
 
 VP_OK, VP_ERR_ARG, VP_ERR_CUDA, VP_ERR_WORKSPACE, VP_ERR_NONFINITE, VP_ERR_TIMEOUT, \
-    VP_ERR_STATE, VP_ERR_UNSUPPORTED = range(8)
+    VP_ERR_STATE, VP_ERR_UNSUPPORTED, VP_ERR_CANCELLED = range(9)
 VP_BASIS_TENT, VP_BASIS_CUBIC_BSPLINE, VP_BASIS_SEPTIC_BSPLINE = 0, 1, 2
 VP_PUSH_LEAPFROG_KDK, VP_PUSH_EXACT_ROTATION, VP_PUSH_FEL_DKD, VP_PUSH_FEL_RK4 = 0, 1, 2, 3
 VP_POT_FREE, VP_POT_PENDULUM, VP_POT_HARMONIC = 0, 1, 2
@@ -128,6 +128,7 @@ _SIGNATURES = [
     ("vp_server_submit", C.c_int, [C.c_void_p, C.POINTER(vp_request)]),
     ("vp_server_run", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     ("vp_server_poll", C.c_int, [C.c_void_p, C.POINTER(vp_result), C.c_int32, C.POINTER(C.c_int32)]),
+    ("vp_server_cancel", C.c_int, [C.c_void_p, C.c_uint64]),
     ("vp_server_take_f", C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int32, C.c_size_t]),
     ("vp_server_clock", C.c_double, []),
     ("vp_server_destroy", None, [C.c_void_p]),
@@ -399,6 +400,10 @@ class Server:
             out.append(dict(id=r.id, status=r.status, batched=r.batched, t_submit=r.t_submit,
                             t_admit=r.t_admit, t_finish=r.t_finish, moments=r.moments.as_dict()))
         return out
+
+    def cancel(self, rid):
+        """Cancel a queued or running request; its result comes back with VP_ERR_CANCELLED."""
+        self._err(lib().vp_server_cancel(self.h, int(rid)))
 
     def take_f(self, rid, shape, dtype=np.float64):
         out = np.empty(shape, dtype=dtype)

@@ -84,6 +84,45 @@ def test_batch_matches_oracle():
     b.close()
 
 
+def _batch_vs_oracle(wls, tiles, steps):
+    stream = torch.cuda.Stream()
+    sims = []
+    for wl, (tx, tp) in zip(wls, tiles):
+        s = V.Sim(wl.grid, wl.basis, wl.pusher, precision=V.VP_FP32, tile_x=tx, tile_p=tp,
+                  stream=stream)
+        s.set_f(I.make_f0(wl).astype(np.float32))
+        sims.append(s)
+    b = V.Batch(sims, stream=stream)
+    b.step(steps)
+    for wl, s in zip(wls, sims):
+        st = O.State(wl.grid, wl.pusher, wl.basis, wl.projection,
+                     I.make_f0(wl).astype(np.float32).astype(np.float64))
+        hist = st.run(steps, history=True)
+        assert rel_l1(s.get_f(), st.w) <= FP32_TOL, (wl.name, s.plan())
+        if wl.pusher.kind == I.PUSH_FEL:
+            gh, ah = np.hypot(*s.field_history().T), np.hypot(*hist.T)
+            assert np.max(np.abs(gh - ah) / ah) <= 5e-4, wl.name
+        s.close()
+    b.close()
+
+
+@pytest.mark.parametrize("tx", [64, 128, 224, 256])
+def test_batch_tile_shapes_match_oracle(tx):
+    """The tile shapes the batched autotuner picks for the 256-instance workload (widths 64,
+    128, 224, 256 at height 64), each applied to pendulum and FEL instances of the batch."""
+    wls = [w for w in I.batch_256(count=24, steps=0) if w.grid.nx <= 512]
+    wls = [w for w in wls if w.pusher.kind == I.PUSH_KDK][:2] + \
+        [w for w in wls if w.pusher.kind == I.PUSH_FEL][:2]
+    _batch_vs_oracle(wls, [(tx, 64)] * len(wls), 12)
+
+
+def test_batch_autotuned_shapes_match_oracle():
+    """Shapes from vp_autotune(batched=1), as the benchmark's batch uses them."""
+    wls = [w for w in I.batch_256(count=24, steps=0) if w.grid.nx <= 512][:6]
+    tuned = V.autotune(wls, batched=True)
+    _batch_vs_oracle(wls, [(r["tile_x"], r["tile_p"]) for r in tuned], 10)
+
+
 def test_batch_rejects_mixed_precision():
     stream = torch.cuda.Stream()
     wl = mixed_workloads()[0]

@@ -1,8 +1,11 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
 Tolerances: FP64 GPU mode <= 1e-12 relative L-infinity (max|d| / max|f_oracle|);
-FP32 mode <= 1e-5 relative L1 (sum|d| / sum|f_oracle|). Field histories are
-compared with the same bounds on |A|.
+FP32 mode <= 1e-5 relative L1 (sum|d| / sum|f_oracle|). FEL field histories: FP64
+within the FP64 bound on |A|; FP32 within 5e-4 relative on |A| (FP32_FIELD_TOL): the
+theta modulation of the initial state is 1e-4 of f, so FP32 rounding of f (about
+1e-7 per value) is a perturbation of order 1e-4 relative of the early bunching and
+hence of A.
 """
 import math
 
@@ -306,3 +309,22 @@ def test_fel_4096x2048_fp32_cubic_few_steps_full_size():
     got, st, _, hist, ohist = run_pair(wl, 3)
     check(got, st.w, I.FP32)
     assert np.max(np.abs(hist - ohist)) <= 1e-6 * np.max(np.hypot(ohist[:, 0], ohist[:, 1]))
+
+
+@pytest.mark.parametrize("tile,steps", [((224, 63), 2), ((224, 60), 1)])
+def test_pendulum_8192_fp32_cubic_at_bench_tiles(tile, steps):
+    """The 8192^2 pendulum at the tile shapes the benchmark times: the autotuner's heights
+    63 and 60 are not multiples of the 16-row p-solve chunk, so the last chunk of every
+    tile column is ragged."""
+    wl = I.pendulum_8192_fp32_cubic()
+    got, st, _, _, _ = run_pair(wl, steps, kernel=V.VP_KERNEL_FUSED, tile=tile)
+    check(got, st.w, I.FP32)
+
+
+def test_pendulum_8192_fp32_cubic_at_the_autotuned_tile():
+    """Exactly the plan the benchmark's headline line uses: the shape the autotuner picks on
+    this device for the 8192^2 pendulum, one step against the oracle."""
+    wl = I.pendulum_8192_fp32_cubic()
+    tuned = V.autotune([wl])[0]
+    got, st, _, _, _ = run_pair(wl, 1, tile=(tuned["tile_x"], tuned["tile_p"]))
+    check(got, st.w, I.FP32)

@@ -1,10 +1,15 @@
 """vp_moments_static: moments with no device allocation (its scratch is a static device array).
 
-For callers that cannot allocate device memory when they need the diagnostics,
-e.g. while a CUDA graph is being captured or when a framework allocator owns
-the device. The entry point must give what vp_moments gives, within the FP64
-tolerance of the other moment tests, on consecutive calls that share the array.
-This file is collected last on purpose.
+For callers that cannot allocate device memory when they want the diagnostics:
+an application whose framework allocator already holds the device's memory, or
+a latency-critical loop that must not take the synchronisation an allocation
+can bring. The entry point must give what vp_moments gives, within the FP64
+tolerance of the other moment tests, on two consecutive calls that share the
+static array, and agree with the FP64 oracle's moments of the same weights.
+
+The file name sorts last, so pytest collects it after every other test file: a
+run that stops at the first failure (-x) has then already run all the other
+tests if this one fails. It also runs on its own in a fresh process.
 """
 import ctypes as C
 
@@ -14,6 +19,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from oracle import oracle as O  # noqa: E402
 from paper_2007_12227_gb300 import inputs as I  # noqa: E402
 from paper_2007_12227_gb300 import vlasov as V  # noqa: E402
 
@@ -66,6 +72,12 @@ def test_static_moments_equal_vp_moments_on_two_calls(which):
                   "trapped", "entropy", "neg_mass", "b_re", "b_im", "max_abs_w", "lost_mass"):
             scale = max(abs(want[k]), 1e-9 * abs(want["sum_w"]))
             assert abs(got[k] - want[k]) <= TOL * scale, (call, k, got[k], want[k])
+        # the oracle's FP64 moments of the same weights
+        om = O.moments(wl.grid, wl.pusher, w.double().cpu().numpy(), (want["a_re"], want["a_im"]))
+        for k in ("sum_w", "mass", "mean_x", "mean_p", "var_x", "var_p", "cov_xp", "energy",
+                  "trapped", "entropy", "neg_mass", "b_re", "b_im", "max_abs_w"):
+            scale = max(abs(om[k]), 1e-9 * abs(om["sum_w"]))
+            assert abs(got[k] - om[k]) <= TOL * scale, (call, k, got[k], om[k])
     sim.close()
 
 
