@@ -35,7 +35,7 @@ UNIT = "node-updates/s"
 FALLBACK_HBM_GBS = 6800.0
 # sources of the one-pass step kernel: the committed ncu traffic applies only to these bytes
 FUSED_SOURCES = ["paper_2007_12227_gb300/csrc/vp_fused.cu", "paper_2007_12227_gb300/csrc/vp_internal.h",
-                 "paper_2007_12227_gb300/csrc/vp_sum.cuh"]
+                 "paper_2007_12227_gb300/csrc/vp_sum.cuh", "paper_2007_12227_gb300/csrc/vp_fel.cuh"]
 
 
 def parse():
@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--serve-count", type=int, default=60,
                     help="requests of the serving trace to run (the whole fixed trace is 2000)")
     ap.add_argument("--tile", default="", help="TX,TP: fixed tile shape instead of the autotuner's")
+    ap.add_argument("--skip-late", action="store_true",
+                    help="skip timing the last 20 steps of the workload's run")
     return ap.parse_args()
 
 
@@ -256,7 +258,23 @@ def bench_batch(V, torch, stream, batch_steps=40, seq_rounds=5):
                          "shapes": sorted({(r["tile_x"], r["tile_p"]) for r in tuned})}}
 
 
-def bench_serve(V, torch, stream, count=60, budget_gb=150.0, rate=500.0):
+def sequential_plain(V, torch, stream, reqs, f0s):
+    """The same requests solved one after another with plain vp_step calls (each: create,
+    set the weights, step, read the moments, destroy): the baseline the served form must beat."""
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for r, f0 in zip(reqs, f0s):
+        sim = V.Sim(r.workload.grid, r.workload.basis, r.workload.pusher, precision=V.VP_FP32,
+                    stream=stream)
+        sim.set_f(f0)
+        sim.step(r.workload.steps)
+        sim.moments()
+        sim.close()
+    torch.cuda.synchronize()
+    return time.perf_counter() - t0
+
+
+def bench_serve(V, torch, stream, count=60, budget_gb=150.0, rate=500.0, sequential=False):
     """Served form: the first `count` requests of the Poisson trace (meshes 128^2 .. 4096^2
     log-uniform, 100 .. 5000 steps, pendulum / FEL) arriving in real time at `rate` per
     second; continuous batching under an HBM budget. Latency = finish - arrival."""
@@ -285,7 +303,13 @@ def bench_serve(V, torch, stream, count=60, budget_gb=150.0, rate=500.0):
     lat = sorted(done[r.rid]["t_finish"] - (t0 + r.arrival) for r in reqs)
     work = sum(r.workload.grid.nodes * r.workload.steps for r in reqs)
     part = "full" if count >= 2000 else "prefix"
+    seq = None
+    if sequential:
+        seq_s = sequential_plain(V, torch, stream, reqs, f0s)
+        seq = {"wall_s": seq_s, "node_updates_per_s": work / seq_s,
+               "served_over_sequential": (work / wall) / (work / seq_s)}
     return {"requests": count, "trace": f"Poisson {rate:.3g}/s, seed 2007122272 ({part})",
+            "sequential_plain": seq,
             "rate_per_s": rate, "offered_node_updates_per_s": rate * work / count,
             "node_updates": work, "wall_s": wall, "node_updates_per_s": work / wall,
             "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
@@ -293,18 +317,36 @@ def bench_serve(V, torch, stream, count=60, budget_gb=150.0, rate=500.0):
             "batched_fraction": sum(1 for d in done.values() if d["batched"]) / len(done)}
 
 
-def cpu_baseline(wl, steps=2):
-    """The FP64 oracle, `steps` steps of the full mesh, single thread (a bounded sample)."""
+def oracle_fel_state(wl, f):
+    if wl.pusher.kind != I.PUSH_FEL:
+        return None
     from oracle import oracle as O
-    f = I.make_f0(wl)
+    br, bi = O.bunching(wl.grid, f)
+    return [wl.pusher.a0_re, wl.pusher.a0_im, br, bi]
+
+
+def cpu_baseline(wl, steps=2):
+    """The FP64 oracle on a bounded sample (`steps` steps of the full mesh): its band-parallel
+    mode over all host cores (bitwise the serial step), and the serial step on one core."""
+    from oracle import oracle as O
+    cores = os.cpu_count() or 1
+    f0 = I.make_f0(wl)
     O.lib()
+    f, fel = f0, oracle_fel_state(wl, f0)
     t0 = time.perf_counter()
     for _ in range(steps):
-        f, _, _ = O.step(wl.grid, wl.basis, I.PROJ_GALERKIN, wl.pusher, f)
-    dt = time.perf_counter() - t0
-    return {"value": wl.grid.nodes * steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{steps} steps of the full {wl.grid.nx}x{wl.grid.np} mesh, FP64 serial C "
-                      f"oracle, {dt:.2f} s"}
+        f, fel, _ = O.step_par(wl.grid, wl.basis, I.PROJ_GALERKIN, wl.pusher, f, fel, threads=cores)
+    dpar = time.perf_counter() - t0
+    f, fel = f0, oracle_fel_state(wl, f0)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        f, fel, _ = O.step(wl.grid, wl.basis, I.PROJ_GALERKIN, wl.pusher, f, fel)
+    dser = time.perf_counter() - t0
+    return {"value": wl.grid.nodes * steps / dpar, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{steps} steps of the full {wl.grid.nx}x{wl.grid.np} mesh, FP64 C oracle in its "
+                      f"band-parallel mode on {cores} threads (bitwise the serial step), {dpar:.2f} s",
+            "serial": {"value": wl.grid.nodes * steps / dser, "cores": 1,
+                       "sample": f"the same {steps} steps, serial, {dser:.2f} s"}}
 
 
 def g_str(wl):
@@ -317,25 +359,28 @@ def run_reference(args):
         return 0
     from oracle import oracle as O
     side = 2048
+    cores = os.cpu_count() or 1
     wl = workload(side, args.workload)
     full = workload(0, args.workload)
     f = I.make_f0(wl)
+    fel = oracle_fel_state(wl, f)
     O.lib()
     for _ in range(args.warmup):
-        f, _, _ = O.step(wl.grid, wl.basis, I.PROJ_GALERKIN, wl.pusher, f)
+        f, fel, _ = O.step_par(wl.grid, wl.basis, I.PROJ_GALERKIN, wl.pusher, f, fel, threads=cores)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        f, _, _ = O.step(wl.grid, wl.basis, I.PROJ_GALERKIN, wl.pusher, f)
+        f, fel, _ = O.step_par(wl.grid, wl.basis, I.PROJ_GALERKIN, wl.pusher, f, fel, threads=cores)
     dt = time.perf_counter() - t0
     value = wl.grid.nodes * args.steps / dt
     sample = (f"{args.steps} steps of the same physics on a {g_str(wl)} mesh "
-              f"(FP64 serial C oracle; full mesh is {g_str(full)})")
+              f"(FP64 C oracle, band-parallel on {cores} threads, bitwise the serial step; "
+              f"full mesh is {g_str(full)})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": full.name, "sample_mesh": g_str(wl), "steps": args.steps},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -411,10 +456,10 @@ def main():
     ms = max_over_ranks(ms, dist, "cuda")
     ms_per_step = ms / args.steps
     value = whole_job_rate(ws, N * args.steps, ms * 1e-3)
-    # kernels per vp_step on this plan: the one-pass step kernel and the step counter
-    # (FEL: the field update); the separate-filter plan adds the two Lambda solves
-    launches_per_step = 2 if sim.kernel() == V.VP_KERNEL_FUSED else 4
+    # kernels per vp_step on this plan, as the library reports it (the one-pass kernel finishes
+    # the step in its last CTA: one launch per step)
     plan = sim.plan()
+    launches_per_step = plan["launches_per_step"]
 
     # ---- per-phase device time (same stream, events between the kernels)
     if cold:
@@ -449,6 +494,26 @@ def main():
                 "phase_ms": dict(zip(names, phase_ms)),
                 "step_algorithmic_gbs": 8 * N / (ms_per_step * 1e-3) / 1e9,
                 "step_frac": 8 * N / (ms_per_step * 1e-3) / 1e9 / peak}
+
+    # ---- late in the run: the last 20 of the workload's 2000 steps (the state filaments, the
+    #      kernel's work depends on it), timed the same way outside the headline region
+    late = None
+    done = args.warmup + args.steps + (min(args.steps, 500) if not cold else 0)
+    if wl.steps >= 40 and not args.skip_late:
+        target = wl.steps - 20
+        if done < target:
+            sim.step(target - done)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        sim.step(20)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        sim.sync()
+        late = {"steps": f"{max(done, target) + 1}-{max(done, target) + 20}",
+                "ms_per_step": ev0.elapsed_time(ev1) / 20,
+                "node_updates_per_s": N * 20 / (ev0.elapsed_time(ev1) * 1e-3),
+                "l2": "steps back to back" if not cold else "steps back to back (working set in L2)"}
 
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
@@ -500,7 +565,7 @@ def main():
     if not args.skip_extra and rank == 0 and not args.skip_batch:
         extra["batch_256"] = bench_batch(V, torch, stream, args.batch_steps)
     if not args.skip_extra and rank == 0 and not args.skip_serve:
-        extra["served"] = bench_serve(V, torch, stream, count=args.serve_count)
+        extra["served"] = bench_serve(V, torch, stream, count=args.serve_count, sequential=True)
         # the same requests at ~70% of the batched throughput: a queue that stays bounded
         cap = extra.get("batch_256", {}).get("batched_node_updates_per_s", 4e10)
         reqs = I.serving_trace(count=args.serve_count)
@@ -530,6 +595,7 @@ def main():
                                   f"inputs larger than L2 (two {4 * N / 2**20:.0f} MiB state buffers + "
                                   f"{4 * N / 2**20:.0f} MiB solve scratch)")},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+                "late_window": late,
                 "gpu_launches": launches_per_step * args.steps, "extra": extra}
         print(json.dumps(line), flush=True)
     sim.close()

@@ -251,8 +251,15 @@ vp_status vp_batch_workspace_size(vp_sim *const *sims, int32_t count, size_t *by
 vp_status vp_batch_create(vp_sim *const *sims, int32_t count, void *stream, void *workspace,
                           size_t workspace_bytes, vp_batch **out);
 /* Advance every simulation of the batch n steps (asynchronous). use_graph = 1
- * replays one captured step graph per step (captured on the first call). */
+ * replays one captured step graph per step (captured on the first call); on the
+ * legacy default stream (stream NULL), which cannot be captured, the steps are
+ * launched directly instead. */
 vp_status vp_batch_step(vp_batch *batch, int32_t n, int32_t use_graph);
+/* As vp_batch_step, but simulation k advances min(n, max_steps[k]) steps (0 or less:
+ * none): the launches of the n steps skip a simulation's tiles once it has taken its
+ * steps, so uneven runs share the launches without splitting the call. max_steps: host
+ * array of the batch's count entries, read before the call returns. */
+vp_status vp_batch_step_each(vp_batch *batch, int32_t n, const int32_t *max_steps, int32_t use_graph);
 vp_status vp_batch_sync(vp_batch *batch);
 void vp_batch_destroy(vp_batch *batch);
 const char *vp_batch_last_error(const vp_batch *batch);

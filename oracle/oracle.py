@@ -51,7 +51,7 @@ def build(force: bool = False) -> str:
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+    cmd = ["gcc", "-O2", "-std=c99", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-pthread",
            "-shared", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
@@ -68,6 +68,9 @@ def lib():
             L.or_step.argtypes = [C.POINTER(OrGrid), C.c_int, C.c_int, C.POINTER(OrPusher),
                                   dp, dp, dp, dp]
             L.or_step.restype = C.c_int
+            L.or_step_par.argtypes = [C.POINTER(OrGrid), C.c_int, C.c_int, C.POINTER(OrPusher),
+                                      dp, dp, dp, dp, C.c_int]
+            L.or_step_par.restype = C.c_int
             L.or_run.argtypes = [C.POINTER(OrGrid), C.c_int, C.c_int, C.POINTER(OrPusher),
                                  dp, dp, C.c_long, dp, dp]
             L.or_run.restype = C.c_int
@@ -145,6 +148,21 @@ def step(grid, basis, projection, pusher, w, fel=None):
                        _dp(w_out), _dp(lost))
     if rc:
         raise RuntimeError(f"or_step failed with code {rc}")
+    return w_out, f, float(lost[0])
+
+
+def step_par(grid, basis, projection, pusher, w, fel=None, threads=None):
+    """One step on `threads` host threads (default: all cores), bitwise equal to step()."""
+    g, pu = _grid(grid), _pusher(pusher)
+    w_in = _arr(w, grid)
+    w_out = np.empty_like(w_in)
+    f = np.zeros(4) if fel is None else np.array(fel, dtype=np.float64).copy()
+    lost = np.zeros(1)
+    nt = threads or os.cpu_count() or 1
+    rc = lib().or_step_par(C.byref(g), int(basis), int(projection), C.byref(pu), _dp(f), _dp(w_in),
+                           _dp(w_out), _dp(lost), int(nt))
+    if rc:
+        raise RuntimeError(f"or_step_par failed with code {rc}")
     return w_out, f, float(lost[0])
 
 

@@ -612,3 +612,264 @@ void or_moments(const or_grid *g, const or_pusher *pu, const double *w,
 }
 
 int or_nmom(void) { return OR_NMOM; }
+
+/* ------------------------------------------------------ band-parallel step
+ *
+ * The same step as or_step, spread over host threads for timing on many cores,
+ * with bitwise the same result: every target cell receives its contributions
+ * in the serial order (sources in row-major order, then the tap loops), only
+ * the target rows are split into bands, one per thread. A thread walks the
+ * source rows whose pushed footprint reaches its band (found by a first
+ * parallel pass over the source rows) and keeps the taps on its own rows. The
+ * weight deposited beyond the momentum range (rows < 0 belong to the first
+ * band, rows >= np to the last) is recorded per source in order and folded
+ * serially in the serial order. The mass-matrix solves run row by row, then
+ * column by column, each row or column with the serial arithmetic. The FEL
+ * bunching is the serial sum. Supported: tent and cubic B-spline deposits,
+ * Galerkin or lumped, every pusher but RK4, no space charge.
+ */
+#include <pthread.h>
+
+typedef struct {
+    long k;      /* source index */
+    double v;    /* its contribution beyond the momentum range */
+} or_lost_item;
+
+typedef struct {
+    const or_grid *g;
+    int basis, projection;
+    const or_pusher *pu;
+    double k_re, k_im;
+    const double *w_in;
+    double *w_out;
+    long *rlo, *rhi;          /* per source row: lowest and highest target row of its taps */
+    int lo, hi;               /* rows (or columns) of this thread */
+    int first, last;          /* the band takes the rows below 0 / from np up */
+    or_lost_item *lost;
+    long nlost, cap;
+    int fail;
+} or_task;
+
+static void push_node(const or_task *t, double x, double p, double *u, double *v)
+{
+    const or_grid *g = t->g;
+    double xf, pf;
+    or_push(t->pu, t->k_re, t->k_im, x, p, &xf, &pf);
+    *u = (xf - g->x0) / grid_hx(g);
+    *v = (pf - g->p0) / grid_hp(g);
+}
+
+static void *pass_rows(void *arg)
+{
+    or_task *t = (or_task *)arg;
+    const or_grid *g = t->g;
+    const double radius = (t->basis == OR_TENT) ? 1.0 : 2.0;
+    const double hx = grid_hx(g), hp = grid_hp(g);
+    for (int j = t->lo; j < t->hi; ++j) {
+        long mn = 0x7fffffffL, mx = -0x7fffffffL;
+        for (int i = 0; i < g->nx; ++i) {
+            if (t->w_in[(long)j * g->nx + i] == 0.0) continue;
+            double u, v;
+            push_node(t, g->x0 + i * hx, g->p0 + j * hp, &u, &v);
+            const long r_lo = (long)ceil(v - radius), r_hi = (long)floor(v + radius);
+            if (r_lo < mn) mn = r_lo;
+            if (r_hi > mx) mx = r_hi;
+        }
+        t->rlo[j] = mn;
+        t->rhi[j] = mx;
+    }
+    return NULL;
+}
+
+static void *pass_deposit(void *arg)
+{
+    or_task *t = (or_task *)arg;
+    const or_grid *g = t->g;
+    const int nx = g->nx, np = g->np;
+    const double radius = (t->basis == OR_TENT) ? 1.0 : 2.0;
+    const double hx = grid_hx(g), hp = grid_hp(g);
+    const long blo = t->first ? -0x7fffffffL : t->lo, bhi = t->last ? 0x7fffffffL : t->hi;
+    for (int j = 0; j < np; ++j) {
+        if (t->rhi[j] < blo || t->rlo[j] >= bhi) continue;
+        const double p = g->p0 + j * hp;
+        for (int i = 0; i < nx; ++i) {
+            const double w = t->w_in[(long)j * nx + i];
+            if (w == 0.0) continue;
+            double u, v;
+            push_node(t, g->x0 + i * hx, p, &u, &v);
+            const long c_lo = (long)ceil(u - radius), c_hi = (long)floor(u + radius);
+            const long r_lo = (long)ceil(v - radius), r_hi = (long)floor(v + radius);
+            for (long rr = r_lo; rr <= r_hi; ++rr) {
+                if (rr < blo || rr >= bhi) continue;
+                const double kp = hp * k_basis(t->basis, rr - v);
+                if (kp == 0.0) continue;
+                for (long cc = c_lo; cc <= c_hi; ++cc) {
+                    const double kx = hx * k_basis(t->basis, cc - u);
+                    const double contrib = kx * kp * w;
+                    if (rr < 0 || rr >= np) {
+                        if (t->nlost == t->cap) {
+                            long nc = t->cap ? 2 * t->cap : 4096;
+                            or_lost_item *nl = (or_lost_item *)realloc(t->lost, sizeof(or_lost_item) * nc);
+                            if (!nl) { t->fail = 1; return NULL; }
+                            t->lost = nl;
+                            t->cap = nc;
+                        }
+                        t->lost[t->nlost].k = (long)j * nx + i;
+                        t->lost[t->nlost].v = contrib;
+                        t->nlost++;
+                        continue;
+                    }
+                    t->w_out[rr * nx + mod_l(cc, nx)] += contrib;
+                }
+            }
+        }
+    }
+    return NULL;
+}
+
+static void *pass_solve_x(void *arg)
+{
+    or_task *t = (or_task *)arg;
+    const or_grid *g = t->g;
+    const double hx = grid_hx(g);
+    double *work = (double *)malloc(sizeof(double) * 4 * (size_t)g->nx);
+    if (!work) { t->fail = 1; return NULL; }
+    for (int j = t->lo; j < t->hi; ++j)
+        cyclic_solve(g->nx, hx / 6.0, 2.0 * hx / 3.0, t->w_out + (long)j * g->nx, work);
+    free(work);
+    return NULL;
+}
+
+static void *pass_solve_p(void *arg)
+{
+    or_task *t = (or_task *)arg;
+    const or_grid *g = t->g;
+    const int nx = g->nx, np = g->np;
+    const double hp = grid_hp(g);
+    double *work = (double *)malloc(sizeof(double) * 3 * (size_t)np);
+    if (!work) { t->fail = 1; return NULL; }
+    double *bd = work, *cp = work + np, *col = work + 2 * np;
+    for (int i = t->lo; i < t->hi; ++i) {
+        for (int j = 0; j < np; ++j) {
+            col[j] = t->w_out[(long)j * nx + i];
+            bd[j] = 2.0 * hp / 3.0;
+        }
+        thomas(np, hp / 6.0, bd, hp / 6.0, col, cp);
+        for (int j = 0; j < np; ++j) t->w_out[(long)j * nx + i] = col[j];
+    }
+    free(work);
+    return NULL;
+}
+
+static void *pass_scale(void *arg)
+{
+    or_task *t = (or_task *)arg;
+    const double inv = 1.0 / (grid_hx(t->g) * grid_hp(t->g));
+    for (long k = (long)t->lo * t->g->nx; k < (long)t->hi * t->g->nx; ++k) t->w_out[k] *= inv;
+    return NULL;
+}
+
+/* run fn over [0, n) split into nthreads contiguous parts */
+static int run_parts(or_task *tasks, int nthreads, int n, void *(*fn)(void *))
+{
+    pthread_t th[256];
+    for (int t = 0; t < nthreads; ++t) {
+        tasks[t].lo = (int)((long)n * t / nthreads);
+        tasks[t].hi = (int)((long)n * (t + 1) / nthreads);
+        tasks[t].first = t == 0;
+        tasks[t].last = t == nthreads - 1;
+    }
+    int started = 0;
+    for (int t = 1; t < nthreads; ++t) {
+        if (pthread_create(&th[t], NULL, fn, &tasks[t]) != 0) break;
+        started = t;
+    }
+    fn(&tasks[0]);
+    for (int t = 1; t <= started; ++t) pthread_join(th[t], NULL);
+    for (int t = started + 1; t < nthreads; ++t) fn(&tasks[t]);   /* threads that did not start */
+    for (int t = 0; t < nthreads; ++t)
+        if (tasks[t].fail) return 1;
+    return 0;
+}
+
+int or_step_par(const or_grid *g, int basis, int projection, const or_pusher *pu,
+                double *fel, const double *w_in, double *w_out, double *lost, int nthreads)
+{
+    const int nx = g->nx, np = g->np;
+    if (nx < 3 || np < 2) return 1;
+    if (basis == OR_SEPTIC || pu->kind == OR_FEL_RK4 || (pu->kind == OR_FEL && pu->sigma2 != 0.0))
+        return 4;
+    if (nthreads < 1) nthreads = 1;
+    if (nthreads > 256) nthreads = 256;
+    const double hx = grid_hx(g), hp = grid_hp(g);
+    const long n = (long)nx * np;
+    double a_re = 0.0, a_im = 0.0;
+    if (pu->kind == OR_FEL) {
+        if (!fel) return 2;
+        a_re = fel[0] + 0.5 * pu->dt * fel[2];
+        a_im = fel[1] + 0.5 * pu->dt * fel[3];
+    }
+    or_task *tasks = (or_task *)calloc((size_t)nthreads, sizeof(or_task));
+    long *rlo = (long *)malloc(sizeof(long) * 2 * (size_t)np);
+    if (!tasks || !rlo) { free(tasks); free(rlo); return 3; }
+    for (int t = 0; t < nthreads; ++t) {
+        tasks[t].g = g;
+        tasks[t].basis = basis;
+        tasks[t].projection = projection;
+        tasks[t].pu = pu;
+        tasks[t].k_re = a_re;
+        tasks[t].k_im = a_im;
+        tasks[t].w_in = w_in;
+        tasks[t].w_out = w_out;
+        tasks[t].rlo = rlo;
+        tasks[t].rhi = rlo + np;
+    }
+    memset(w_out, 0, sizeof(double) * n);
+    int rc = run_parts(tasks, nthreads, np, pass_rows);
+    if (!rc) rc = run_parts(tasks, nthreads, np, pass_deposit);
+    /* lost weight in the serial order: by source, the first band's rows before the last's */
+    double lost_acc = 0.0;
+    if (!rc) {
+        const or_task *a = &tasks[0], *b = &tasks[nthreads - 1];
+        long ia = 0, ib = 0;
+        if (nthreads == 1) {
+            for (; ia < a->nlost; ++ia) lost_acc += a->lost[ia].v;
+        } else {
+            while (ia < a->nlost || ib < b->nlost) {
+                if (ib >= b->nlost || (ia < a->nlost && a->lost[ia].k <= b->lost[ib].k))
+                    lost_acc += a->lost[ia++].v;
+                else
+                    lost_acc += b->lost[ib++].v;
+            }
+        }
+    }
+    for (int t = 0; t < nthreads; ++t) free(tasks[t].lost);
+    if (!rc) {
+        if (basis == OR_CUBIC && projection == OR_GALERKIN) {
+            rc = run_parts(tasks, nthreads, np, pass_solve_x);
+            if (!rc) rc = run_parts(tasks, nthreads, nx, pass_solve_p);
+        } else {
+            rc = run_parts(tasks, nthreads, np, pass_scale);
+        }
+    }
+    free(tasks);
+    free(rlo);
+    if (rc) return 3;
+    if (lost) *lost += lost_acc / (hx * hp);
+    if (pu->kind == OR_FEL) {
+        double s = 0.0, sc = 0.0, ss = 0.0;
+        for (int j = 0; j < np; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const double w = w_out[(long)j * nx + i];
+                const double th = g->x0 + i * hx;
+                s += w;
+                sc += w * cos(th);
+                ss += w * sin(th);
+            }
+        fel[2] = sc / s;
+        fel[3] = -ss / s;
+        fel[0] = a_re + 0.5 * pu->dt * fel[2];
+        fel[1] = a_im + 0.5 * pu->dt * fel[3];
+    }
+    return 0;
+}

@@ -30,7 +30,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 struct Layout {
     size_t f0, f1, tmp, col, row, rowb, vcb, rowbf, vcbf, csx, ucol, vcol, piv, ldl, sigma, smax, tsrc, rtil,
         state, hist,
-        lost, part, mpart, mout, err, total;
+        lost, part, mpart, mout, err, ticket, total;
 };
 
 struct Plan {
@@ -271,6 +271,7 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     L.mpart = take((size_t)P->nmblk * kNumMoments * sizeof(double));
     L.mout = take(kMoutLen * sizeof(double));
     L.err = take(sizeof(unsigned));
+    L.ticket = take(kernel == VP_KERNEL_FUSED ? sizeof(int) : 0);
     L.total = off;
     return VP_OK;
 }
@@ -390,6 +391,9 @@ FusedArgs<T> fused_args(vp_sim *s, const void *src, void *dst)
     a.ws = P.ws;
     a.full_row = P.full_row ? 1 : 0;
     a.fel_partials = P.fel ? 1 : 0;
+    a.ticket = s->ptr<int>(P.L.ticket);
+    a.hist = s->ptr<double>(P.L.hist);
+    a.hist_cap = P.hist_cap;
     return a;
 }
 
@@ -508,14 +512,16 @@ vp_status do_steps(vp_sim *s, int n, cudaEvent_t *ev = nullptr)
             VP_CUDA(s, cudaEventRecord(e[2], s->stream));
             VP_CUDA(s, cudaEventRecord(e[3], s->stream));
         }
+        // the one-pass kernel finishes the step itself (its last CTA: field update or step count)
         if (P.fel) {
-            VP_CUDA(s, launch_fel_finalize(part, nparts, state, s->ptr<double>(P.L.hist), P.hist_cap,
-                                           P.g.dt, 0, s->stream, P.rk4 ? 1 : 0));
+            if (P.kernel != VP_KERNEL_FUSED)
+                VP_CUDA(s, launch_fel_finalize(part, nparts, state, s->ptr<double>(P.L.hist), P.hist_cap,
+                                               P.g.dt, 0, s->stream, P.rk4 ? 1 : 0));
             if (P.g.sigma2 != 0.0 && !P.rk4) {
                 const vp_status sc = fel_space_charge<T>(s, dst);
                 if (sc != VP_OK) return sc;
             }
-        } else {
+        } else if (P.kernel != VP_KERNEL_FUSED) {
             VP_CUDA(s, launch_count_step(state, P.g.dt, s->stream));
         }
         if (e) VP_CUDA(s, cudaEventRecord(e[4], s->stream));
@@ -534,6 +540,7 @@ vp_status reset_state(vp_sim *s, const void *w)
                                cudaMemcpyHostToDevice, s->stream));
     VP_CUDA(s, cudaMemsetAsync(s->ws + P.L.lost, 0, P.nlost * sizeof(double), s->stream));
     VP_CUDA(s, cudaMemsetAsync(s->ws + P.L.err, 0, sizeof(unsigned), s->stream));
+    if (P.kernel == VP_KERNEL_FUSED) VP_CUDA(s, cudaMemsetAsync(s->ws + P.L.ticket, 0, sizeof(int), s->stream));
     VP_CUDA(s, cudaMemsetAsync(s->ws + P.L.hist, 0, (size_t)P.hist_cap * 2 * sizeof(double), s->stream));
     if (P.fel) {
         vp_status st = P.precision == VP_FP64 ? fel_bunching<double>(s, w, 1)
@@ -768,6 +775,8 @@ vp_status vp_create(const vp_grid *grid, int32_t basis, const vp_pusher *pusher,
         e = cudaMemcpyAsync(s->ws + P.L.piv, piv.data(), piv.size() * sizeof(double),
                             cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->ws + P.L.err, 0, sizeof(unsigned), s->stream);
+    if (e == cudaSuccess && P.kernel == VP_KERNEL_FUSED)
+        e = cudaMemsetAsync(s->ws + P.L.ticket, 0, sizeof(int), s->stream);
     // tile source rectangles not computed yet (each entry 0x80808080 = kTileSrcUnset)
     if (e == cudaSuccess && P.kernel == VP_KERNEL_FUSED && !P.fel)
         e = cudaMemsetAsync(s->ws + P.L.tsrc, 0x80, (size_t)P.ntx * P.ntp * sizeof(int4), s->stream);
@@ -1084,8 +1093,10 @@ vp_status vp_plan(const vp_sim *s, vp_plan_info *out)
     out->threads = P.kernel == VP_KERNEL_FUSED ? P.threads : 0;
     out->full_row = P.full_row ? 1 : 0;
     out->state_is_s = P.state_s ? 1 : 0;
-    // step kernel (+ filters along x and p) (+ FEL partials) + field update or step counter
-    int n = 2;
+    // step kernel (+ filters along x and p) (+ FEL partials) + field update or step counter;
+    // the one-pass kernel does the field update or the count in its last CTA
+    int n = P.kernel == VP_KERNEL_FUSED ? 1 : 2;
+    if (P.kernel == VP_KERNEL_FUSED && P.fel && P.g.sigma2 != 0.0) n += 2;   // space-charge kick
     if (P.kernel != VP_KERNEL_FUSED && (P.galerkin || P.septic_gal)) n += 2;
     if (P.septic_gal && P.fel) n += 1;   // FEL partial sums after the septic solves
     if (P.kernel == VP_KERNEL_SCATTER && P.fel && !P.galerkin) n += 1;
@@ -1117,19 +1128,21 @@ struct vp_batch {
     int *d_parity;
     int2 *d_items;
     int *d_counter;
+    int *d_left;            // per simulation: steps it still takes in the current call
     BatchFinal *d_fin;
     int nitems, ninst, threads, grid, basis, projection;
     size_t smem;
     cudaGraphExec_t graph;
     bool have_graph;
     std::vector<int> host_parity;
+    std::vector<int> host_left;
     char msg[512];
 };
 
 namespace {
 
 struct BatchLayout {
-    size_t args, parity, items, counter, fin, total;
+    size_t args, parity, items, counter, left, fin, total;
 };
 
 void batch_layout_of(int count, int items, BatchLayout *L);
@@ -1170,6 +1183,7 @@ void batch_layout_of(int count, int items, BatchLayout *L)
     L->parity = take(sizeof(int) * count);
     L->items = take(sizeof(int2) * items);
     L->counter = take(sizeof(int) * 4);
+    L->left = take(sizeof(int) * count);
     L->fin = take(sizeof(BatchFinal) * count);
     L->total = off;
 }
@@ -1184,10 +1198,10 @@ void batch_layout_of(int count, int items, BatchLayout *L)
 vp_status batch_enqueue_step(vp_batch *b)
 {
     VP_BCUDA(b, cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream));
-    VP_BCUDA(b, launch_step_fused_batch<float>(b->d_args, b->d_parity, b->d_items, b->nitems,
+    VP_BCUDA(b, launch_step_fused_batch<float>(b->d_args, b->d_parity, b->d_left, b->d_items, b->nitems,
                                                b->d_counter, b->basis, b->projection, b->smem,
                                                b->threads, b->grid, b->stream));
-    VP_BCUDA(b, launch_batch_finalize(b->d_fin, b->ninst, b->d_parity, b->stream));
+    VP_BCUDA(b, launch_batch_finalize(b->d_fin, b->ninst, b->d_parity, b->d_left, b->stream));
     return VP_OK;
 }
 
@@ -1237,6 +1251,7 @@ vp_status vp_batch_create(vp_sim *const *sims, int32_t count, void *stream, void
     b->d_parity = reinterpret_cast<int *>(b->ws + L.parity);
     b->d_items = reinterpret_cast<int2 *>(b->ws + L.items);
     b->d_counter = reinterpret_cast<int *>(b->ws + L.counter);
+    b->d_left = reinterpret_cast<int *>(b->ws + L.left);
     b->d_fin = reinterpret_cast<BatchFinal *>(b->ws + L.fin);
     b->nitems = nitems;
     b->ninst = count;
@@ -1254,6 +1269,9 @@ vp_status vp_batch_create(vp_sim *const *sims, int32_t count, void *stream, void
         const Plan &P = s->P;
         args[2 * k] = fused_args<float>(s, s->f(0), s->f(1));
         args[2 * k + 1] = fused_args<float>(s, s->f(1), s->f(0));
+        // the batch finishes every simulation's step in its own finalize launch
+        args[2 * k].ticket = nullptr;
+        args[2 * k + 1].ticket = nullptr;
         b->threads = std::max(b->threads, P.threads);
         order[k] = k;
         fin[k].state = s->ptr<double>(P.L.state);
@@ -1298,7 +1316,7 @@ vp_status vp_batch_create(vp_sim *const *sims, int32_t count, void *stream, void
     per_sm = b->smem > 0 ? (int)std::min<size_t>(2, (size_t)(224 * 1024) / (b->smem + 2048)) : 2;
     if (per_sm < 1) per_sm = 1;
     b->grid = std::max(1, std::min(nitems, nsm * per_sm));
-    e = launch_step_fused_batch<float>(nullptr, nullptr, nullptr, 0, nullptr, b->basis, b->projection,
+    e = launch_step_fused_batch<float>(nullptr, nullptr, nullptr, nullptr, 0, nullptr, b->basis, b->projection,
                                        b->smem, b->threads, 0, b->stream);
     if (e != cudaSuccess) {
         delete b;
@@ -1308,17 +1326,26 @@ vp_status vp_batch_create(vp_sim *const *sims, int32_t count, void *stream, void
     return VP_OK;
 }
 
-vp_status vp_batch_step(vp_batch *b, int32_t n, int32_t use_graph)
+// n steps of the batch; simulation k takes min(n, limit[k]) of them (limit NULL: all n)
+static vp_status batch_steps(vp_batch *b, int32_t n, const int32_t *limit, int32_t use_graph)
 {
     if (!b) return VP_ERR_ARG;
     if (n < 0) return fail(b->msg, VP_ERR_ARG, "negative step count");
     b->host_parity.resize(b->ninst);
+    b->host_left.resize(b->ninst);
     for (int k = 0; k < b->ninst; ++k) {
-        if (!b->sims[k]->f_set) return fail(b->msg, VP_ERR_STATE, "simulation %d has no weights", k);
+        const int take = limit ? std::max(0, std::min(n, limit[k])) : n;
+        if (take > 0 && !b->sims[k]->f_set)
+            return fail(b->msg, VP_ERR_STATE, "simulation %d has no weights", k);
         b->host_parity[k] = b->sims[k]->cur;
+        b->host_left[k] = take;
     }
     VP_BCUDA(b, cudaMemcpyAsync(b->d_parity, b->host_parity.data(), sizeof(int) * b->ninst,
                                 cudaMemcpyHostToDevice, b->stream));
+    VP_BCUDA(b, cudaMemcpyAsync(b->d_left, b->host_left.data(), sizeof(int) * b->ninst,
+                                cudaMemcpyHostToDevice, b->stream));
+    // the legacy default stream cannot be captured: there the steps are launched directly
+    if (b->stream == nullptr) use_graph = 0;
     if (use_graph && n > 0 && !b->have_graph) {
         cudaGraph_t g;
         VP_BCUDA(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
@@ -1340,10 +1367,21 @@ vp_status vp_batch_step(vp_batch *b, int32_t n, int32_t use_graph)
         }
     }
     // host copies of the buffer parity follow the device ones
-    for (int k = 0; k < b->ninst; ++k) b->sims[k]->cur = (b->sims[k]->cur + n) & 1;
-    // the parity upload above reads host memory: complete it before the vector is reused
+    for (int k = 0; k < b->ninst; ++k) b->sims[k]->cur = (b->sims[k]->cur + b->host_left[k]) & 1;
+    // the uploads above read host memory: complete them before the vectors are reused
     VP_BCUDA(b, cudaStreamSynchronize(b->stream));
     return VP_OK;
+}
+
+vp_status vp_batch_step(vp_batch *b, int32_t n, int32_t use_graph)
+{
+    return batch_steps(b, n, nullptr, use_graph);
+}
+
+vp_status vp_batch_step_each(vp_batch *b, int32_t n, const int32_t *max_steps, int32_t use_graph)
+{
+    if (!b || !max_steps) return VP_ERR_ARG;
+    return batch_steps(b, n, max_steps, use_graph);
 }
 
 vp_status vp_batch_sync(vp_batch *b)

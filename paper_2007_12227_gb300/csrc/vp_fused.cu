@@ -31,6 +31,7 @@
 // tile is stored once.
 #include <math.h>
 
+#include "vp_fel.cuh"
 #include "vp_internal.h"
 #include "vp_sum.cuh"
 
@@ -65,6 +66,11 @@ struct FTaps<T, VP_BASIS_TENT> {
     }
 };
 
+// FP32: three weights on the grid 2^-23, the fourth one minus them, so that the four sum to
+// exactly one (see node_taps_f32); FP64: the fourth from the other three
+__device__ __forceinline__ float grid23(float x) { return __fadd_rn(__fadd_rn(x, 1.f), -1.f); }
+__device__ __forceinline__ double grid23(double x) { return x; }
+
 template <typename T>
 struct FTaps<T, VP_BASIS_CUBIC_BSPLINE> {
     static constexpr int N = 4;
@@ -76,13 +82,12 @@ struct FTaps<T, VP_BASIS_CUBIC_BSPLINE> {
         const T t2 = t * t, s2 = s * s;
         const T t3 = t2 * t, s3 = s2 * s;
         const T sixth = T(1) / T(6), two3 = T(2) / T(3);
-        w[0] = s3 * sixth;
-        w[3] = t3 * sixth;
-        w[1] = two3 - t2 + T(0.5) * t3;
-        // the weights sum to one up to unbiased rounding: forming w[2] from the formula
-        // instead would carry the rounding of 2/3 (FP32: a mean excess of 4e-8 per axis)
-        // into the mass of every step
-        w[2] = (T(1) - (w[0] + w[3])) - w[1];
+        w[0] = grid23(s3 * sixth);
+        w[3] = grid23(t3 * sixth);
+        w[1] = grid23(two3 - t2 + T(0.5) * t3);
+        // the weights sum to one: forming w[2] from the formula instead would carry the rounding
+        // of 2/3 (FP32: a mean excess of 4e-8 per axis) into the mass of every step
+        w[2] = ((T(1) - w[0]) - w[3]) - w[1];
     }
 };
 
@@ -130,25 +135,6 @@ __device__ void sin_range32(float lo, float hi, float &smin, float &smax)
         smax = 1.f;
     if ((a <= h3 + 1e-4f && h3 - 1e-4f <= b) || (a <= h3 + twopi + 1e-4f && h3 + twopi - 1e-4f <= b))
         smin = -1.f;
-}
-
-// range of sin over [lo, hi]: FP64 reduction, FP32 evaluation, 1e-5 slack
-__device__ void sin_range_f(double lo, double hi, float &smin, float &smax)
-{
-    const double twopi = 6.283185307179586476925286766559;
-    if (hi - lo >= twopi) {
-        smin = -1.f;
-        smax = 1.f;
-        return;
-    }
-    const double k = floor(lo / twopi);
-    const double a = lo - k * twopi, b = hi - k * twopi;
-    const float sa = sinf((float)a), sb = sinf((float)b);
-    smin = fminf(sa, sb) - 1e-5f;
-    smax = fmaxf(sa, sb) + 1e-5f;
-    const double h1 = 1.5707963267948966, h3 = 4.7123889803846897;
-    if ((a <= h1 && h1 <= b) || (a <= h1 + twopi && h1 + twopi <= b)) smax = 1.f;
-    if ((a <= h3 && h3 <= b) || (a <= h3 + twopi && h3 + twopi <= b)) smin = -1.f;
 }
 
 // Window cells. FP32: fixed-point integers at a per-tile scale, so that the deposit uses
@@ -439,10 +425,16 @@ __device__ __forceinline__ void node_taps_f32(const ColC<float> &c, const RowEnt
         const f2_t T3 = f2_mul(T2, T), S3 = f2_mul(S2, S);
         const float sixth = 1.f / 6.f, two3 = 2.f / 3.f;
         const f2_t SIX = f2_pack(sixth, sixth);
-        const f2_t W0 = f2_mul(S3, SIX), W3 = f2_mul(T3, SIX);
-        const f2_t W1 = f2_fma(T3, f2_pack(0.5f, 0.5f), f2_fma(T2, M1, f2_pack(two3, two3)));
-        // the weights sum to one up to unbiased rounding (as in the scalar form)
-        const f2_t W2 = f2_fma(W1, M1, f2_fma(f2_add(W0, W3), M1, ONE));
+        // three weights rounded to multiples of 2^-23 ((x + 1) - 1), the fourth 1 minus them:
+        // every step is then exact and the four sum to exactly one, so the step keeps the mass
+        // up to unbiased rounding whatever the fractions (a pushed node at t = 0, as in a slow
+        // or resting flow, would otherwise lose 2^-26 of its weight per axis and step)
+        const f2_t MONE = f2_pack(-1.f, -1.f);
+        const f2_t W0 = f2_add(f2_add(f2_mul(S3, SIX), ONE), MONE);
+        const f2_t W3 = f2_add(f2_add(f2_mul(T3, SIX), ONE), MONE);
+        const f2_t W1 = f2_add(f2_add(f2_fma(T3, f2_pack(0.5f, 0.5f), f2_fma(T2, M1, f2_pack(two3, two3))),
+                                      ONE), MONE);
+        const f2_t W2 = f2_fma(W1, M1, f2_fma(W3, M1, f2_fma(W0, M1, ONE)));
         f2_unpack(W0, wx[0], wy[0]);
         f2_unpack(W1, wx[1], wy[1]);
         f2_unpack(W2, wx[2], wy[2]);
@@ -927,9 +919,16 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
             qs = T(0);   // a non-finite state, reported when it was written: its deposit is dropped
             iq = T(0);
         } else {
+            // the scale is a power of two, so that iq = 1 / qs is exact (a rounded iq scales the
+            // tile's weights by 1 +- 6e-8, a gain that repeats over the steps while the tile's
+            // maximum stays put): qs = 2^(32 - e) with m = f 2^e, f in [0.5, 1), i.e. qs m in
+            // [2^31, 2^32): a cell reaches 2^31 only at 4 to 8 times the largest weight (16 to 32
+            // times with the Thomas gain bound), against about one for an area-preserving flow
             const float m = fmaxf(__int_as_float(s_smax), 1e-30f) * (GAL ? 3.1f : 1.f) * 8.f;
-            qs = (T)(2147483648.0f / m);
-            iq = T(1) / qs;
+            int e2;
+            frexpf(m, &e2);
+            qs = (T)ldexpf(1.f, 32 - e2);
+            iq = (T)ldexpf(1.f, e2 - 32);
         }
     }
 
@@ -1148,12 +1147,43 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
     }
 }
 
+// The end of a single simulation's step, in the same launch: each CTA takes a ticket once its
+// tile's partial sums are visible device-wide (thread 0 wrote them, then fences); the CTA that
+// draws the last ticket sees every partial and finishes the step: the FEL field update from all
+// tile partials in the fixed order of fel_finalize_core (the window's shared memory, no longer
+// needed, is its scratch), else the step count. It then resets the counter for the next launch.
+// No CTA waits on another.
+template <typename T>
+__device__ __forceinline__ void finish_step(const FusedArgs<T> &A, unsigned char *smem_raw)
+{
+    __shared__ int s_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        s_last = atomicAdd(A.ticket, 1) == (int)gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double *state = const_cast<double *>(A.state);
+    if (A.fel_partials) {
+        fel_finalize_core(A.tile_part, A.ntx * A.ntp, state, A.hist, A.hist_cap, A.g.dt, 0, 0,
+                          reinterpret_cast<double *>(smem_raw));
+    } else if (threadIdx.x == 0) {
+        const double st = state[ST_STEP] + 1.0;
+        state[ST_STEP] = st;
+        state[ST_TAU] = st * A.g.dt;
+    }
+    if (threadIdx.x == 0) *A.ticket = 0;
+}
+
 template <typename T, int BASIS, bool GAL, bool UTERM, int MINB>
 __global__ void __launch_bounds__(MINB == 1 ? kFusedMaxThreads : kFusedThreads2, MINB)
     step_fused_kernel(const FusedArgs<T> A)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     fused_tile<T, BASIS, GAL, UTERM>(A, blockIdx.x, smem_raw);
+    if (A.ticket) finish_step<T>(A, smem_raw);
 }
 
 // Persistent batched step: CTAs take (instance, tile) items from a counter; instance k
@@ -1161,7 +1191,8 @@ __global__ void __launch_bounds__(MINB == 1 ? kFusedMaxThreads : kFusedThreads2,
 template <typename T, int BASIS, bool GAL, bool UTERM, int MINB>
 __global__ void __launch_bounds__(MINB == 1 ? kFusedMaxThreads : kFusedThreads2, MINB)
     step_fused_batch_kernel(const FusedArgs<T> *__restrict__ args, const int *__restrict__ parity,
-                            const int2 *__restrict__ items, int nitems, int *counter)
+                            const int *__restrict__ left, const int2 *__restrict__ items, int nitems,
+                            int *counter)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(16) FusedArgs<T> sA;
@@ -1172,6 +1203,11 @@ __global__ void __launch_bounds__(MINB == 1 ? kFusedMaxThreads : kFusedThreads2,
         const int it = s_item;
         if (it >= nitems) break;
         const int2 e = items[it];
+        if (left[e.x] <= 0) {
+            // this simulation takes no more steps in this call: skip its tile
+            __syncthreads();
+            continue;
+        }
         const FusedArgs<T> *src = args + 2 * e.x + parity[e.x];
         constexpr int nwords = sizeof(FusedArgs<T>) / 4;
         for (int k = threadIdx.x; k < nwords; k += blockDim.x)
@@ -1192,7 +1228,10 @@ template <typename T>
 cudaError_t launch_step_fused(const FusedArgs<T> &a, int threads, cudaStream_t s)
 {
     const int wh = a.tp + 2 * a.Gp;
-    const size_t smem = fused_smem_bytes<T>(a.ws, wh, threads);
+    // the last CTA's field update uses the window memory as its scratch
+    const size_t smem_tile = fused_smem_bytes<T>(a.ws, wh, threads);
+    const size_t smem_fin = (size_t)3 * kFinThreads * sizeof(double);
+    const size_t smem = smem_tile > smem_fin ? smem_tile : smem_fin;
     const int grid = a.ntx * a.ntp;
     const bool gal = a.g.basis == VP_BASIS_CUBIC_BSPLINE && a.g.projection == VP_PROJ_GALERKIN;
     const bool uterm = a.g.kind == VP_PUSH_FEL_DKD;
@@ -1288,9 +1327,9 @@ cudaError_t launch_lambda_p_mul(const T *w, T *s, int nx, int np, cudaStream_t s
 }
 
 template <typename T>
-cudaError_t launch_step_fused_batch(const FusedArgs<T> *args, const int *parity, const int2 *items,
-                                    int nitems, int *counter, int basis, int projection,
-                                    size_t smem, int threads, int grid, cudaStream_t s)
+cudaError_t launch_step_fused_batch(const FusedArgs<T> *args, const int *parity, const int *left,
+                                    const int2 *items, int nitems, int *counter, int basis,
+                                    int projection, size_t smem, int threads, int grid, cudaStream_t s)
 {
     const bool gal = basis == VP_BASIS_CUBIC_BSPLINE && projection == VP_PROJ_GALERKIN;
 #define VP_LAUNCH_BATCH(B, GL)                                                                \
@@ -1300,7 +1339,7 @@ cudaError_t launch_step_fused_batch(const FusedArgs<T> *args, const int *parity,
         if (grid <= 0) /* set-up call: shared-memory attribute only (not capturable) */       \
             return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
                                         (int)smem);                                           \
-        k<<<grid, threads, smem, s>>>(args, parity, items, nitems, counter);                  \
+        k<<<grid, threads, smem, s>>>(args, parity, left, items, nitems, counter);            \
     } while (0)
     if (basis == VP_BASIS_TENT) VP_LAUNCH_BATCH(VP_BASIS_TENT, false);
     else if (!gal) VP_LAUNCH_BATCH(VP_BASIS_CUBIC_BSPLINE, false);
@@ -1309,10 +1348,10 @@ cudaError_t launch_step_fused_batch(const FusedArgs<T> *args, const int *parity,
     return cudaGetLastError();
 }
 
-template cudaError_t launch_step_fused_batch<float>(const FusedArgs<float> *, const int *, const int2 *,
-                                                    int, int *, int, int, size_t, int, int,
-                                                    cudaStream_t);
-template cudaError_t launch_step_fused_batch<double>(const FusedArgs<double> *, const int *,
+template cudaError_t launch_step_fused_batch<float>(const FusedArgs<float> *, const int *, const int *,
+                                                    const int2 *, int, int *, int, int, size_t, int,
+                                                    int, cudaStream_t);
+template cudaError_t launch_step_fused_batch<double>(const FusedArgs<double> *, const int *, const int *,
                                                      const int2 *, int, int *, int, int, size_t, int,
                                                      int, cudaStream_t);
 template size_t fused_smem_bytes<float>(int, int, int);

@@ -124,6 +124,12 @@ struct FusedArgs {
     // source rectangle (ia, ib, ja, jb) per tile when the push does not change between steps
     // (NULL for the FEL); entries equal to kTileSrcUnset are computed and stored by the tile
     int4 *tile_src;
+    // end of the step in the same launch: every CTA takes a ticket after its tile's partial sums
+    // are visible; the CTA that draws the last one updates the FEL field from all partials (or
+    // counts the step) and resets the counter. NULL: the caller finishes the step (batches).
+    int *ticket;
+    double *hist;           // FEL field history ring (hist_cap steps)
+    int hist_cap;
 };
 constexpr int kTileSrcUnset = (int)0x80808080;   // the bytes 0x80 (cudaMemset)
 
@@ -178,10 +184,11 @@ template <typename T>
 cudaError_t launch_step_fused(const FusedArgs<T> &a, int threads, cudaStream_t s);
 template <typename T>
 size_t fused_smem_bytes(int ws, int wh, int threads);
+// left[k]: steps simulation k still takes in this call; its items are skipped at 0
 template <typename T>
-cudaError_t launch_step_fused_batch(const FusedArgs<T> *args, const int *parity, const int2 *items,
-                                    int nitems, int *counter, int basis, int projection,
-                                    size_t smem, int threads, int grid, cudaStream_t s);
+cudaError_t launch_step_fused_batch(const FusedArgs<T> *args, const int *parity, const int *left,
+                                    const int2 *items, int nitems, int *counter, int basis,
+                                    int projection, size_t smem, int threads, int grid, cudaStream_t s);
 
 // per-instance end-of-step work of a batch: FEL field update, or the step counter
 struct BatchFinal {
@@ -191,7 +198,8 @@ struct BatchFinal {
     int nparts, hist_cap, fel;
     double dt;
 };
-cudaError_t launch_batch_finalize(const BatchFinal *fin, int ninst, int *parity, cudaStream_t s);
+// finishes the step of every simulation with left[k] > 0, flips its parity, decrements left[k]
+cudaError_t launch_batch_finalize(const BatchFinal *fin, int ninst, int *parity, int *left, cudaStream_t s);
 // device bytes of a batch of `count` simulations with `items` tiles in all
 size_t batch_workspace_bytes(int count, int items);
 constexpr int fused_halo(int precision) { return precision == VP_FP64 ? 28 : 16; }

@@ -13,12 +13,14 @@
 #include <math.h>
 
 #include "vp_internal.h"
+#include "vp_fel.cuh"
 #include "vp_sum.cuh"
 
 namespace vp {
 namespace {
 
 constexpr int kRedThreads = 256;
+static_assert(kRedThreads == kFinThreads, "the finalize kernels run one block of kFinThreads threads");
 
 // one block per 32-column strip x row chunk: column sums (compensated) then x cos/sin
 constexpr int kFelRows = 256;
@@ -130,62 +132,12 @@ __global__ void fel_kick_kernel(const double *__restrict__ part, int nparts, dou
     state[ST_PHI] = atan2(kr, -ki);
 }
 
-// FEL field update from per-block partial sums (run by one block)
+// FEL field update from per-block partial sums (run by one block of kFinThreads threads)
 __device__ void fel_finalize_block(const double *__restrict__ part, int nparts, double *state,
                                    double *hist, int hist_cap, double dt, int init, int rk4 = 0)
 {
-    __shared__ double s[3][kRedThreads];
-    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    for (int k = threadIdx.x; k < nparts; k += blockDim.x) {
-        a0 += part[3 * k];
-        a1 += part[3 * k + 1];
-        a2 += part[3 * k + 2];
-    }
-    s[0][threadIdx.x] = a0;
-    s[1][threadIdx.x] = a1;
-    s[2][threadIdx.x] = a2;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if ((int)threadIdx.x < o)
-            for (int q = 0; q < 3; ++q) s[q][threadIdx.x] += s[q][threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x != 0) return;
-    const double sw = s[0][0];
-    const double b_re = s[1][0] / sw, b_im = -s[2][0] / sw;
-    state[ST_B_RE] = b_re;
-    state[ST_B_IM] = b_im;
-    if (init) {
-        // A^0 already stored; A^{1/2} = A^0 + h/2 b^0
-        state[ST_AH_RE] = state[ST_A_RE] + 0.5 * dt * b_re;
-        state[ST_AH_IM] = state[ST_A_IM] + 0.5 * dt * b_im;
-        // kick amplitude K = A^{1/2} (space charge adds i sigma2 <e^{-i theta~}> afterwards)
-        state[ST_K_RE] = state[ST_AH_RE];
-        state[ST_K_IM] = state[ST_AH_IM];
-        state[ST_M] = hypot(state[ST_AH_RE], state[ST_AH_IM]);
-        state[ST_PHI] = atan2(state[ST_AH_RE], -state[ST_AH_IM]);
-        return;
-    }
-    // DKD: A^{n+1} = A^{n+1/2} + h/2 b^{n+1}; RK4: the stages left A^{n+1} in ST_AH
-    const double are = rk4 ? state[ST_AH_RE] : state[ST_AH_RE] + 0.5 * dt * b_re;
-    const double aim = rk4 ? state[ST_AH_IM] : state[ST_AH_IM] + 0.5 * dt * b_im;
-    state[ST_A_RE] = are;
-    state[ST_A_IM] = aim;
-    state[ST_AH_RE] = are + 0.5 * dt * b_re;
-    state[ST_AH_IM] = aim + 0.5 * dt * b_im;
-    state[ST_K_RE] = state[ST_AH_RE];
-    state[ST_K_IM] = state[ST_AH_IM];
-    // sine-term weights of the next push: alpha = -Im K, beta = Re K
-    state[ST_M] = hypot(state[ST_AH_RE], state[ST_AH_IM]);
-    state[ST_PHI] = atan2(state[ST_AH_RE], -state[ST_AH_IM]);
-    const long step = (long)state[ST_STEP];
-    if (hist && hist_cap > 0) {
-        const long slot = step % hist_cap;
-        hist[2 * slot] = are;
-        hist[2 * slot + 1] = aim;
-    }
-    state[ST_STEP] = (double)(step + 1);
-    state[ST_TAU] = (double)(step + 1) * dt;
+    __shared__ double s[3 * kFinThreads];
+    fel_finalize_core(part, nparts, state, hist, hist_cap, dt, init, rk4, s);
 }
 
 __global__ void fel_finalize_kernel(const double *__restrict__ part, int nparts, double *state,
@@ -194,9 +146,11 @@ __global__ void fel_finalize_kernel(const double *__restrict__ part, int nparts,
     fel_finalize_block(part, nparts, state, hist, hist_cap, dt, init, rk4);
 }
 
-// end of a batched step: block k finishes instance k and flips its buffer parity
-__global__ void batch_finalize_kernel(const BatchFinal *__restrict__ fin, int *parity)
+// end of a batched step: block k finishes instance k, flips its buffer parity and counts down
+// the steps it still takes in this call (instances already at zero are left alone)
+__global__ void batch_finalize_kernel(const BatchFinal *__restrict__ fin, int *parity, int *left)
 {
+    if (left[blockIdx.x] <= 0) return;
     const BatchFinal f = fin[blockIdx.x];
     if (f.fel) {
         fel_finalize_block(f.part, f.nparts, f.state, f.hist, f.hist_cap, f.dt, 0);
@@ -205,7 +159,11 @@ __global__ void batch_finalize_kernel(const BatchFinal *__restrict__ fin, int *p
         f.state[ST_STEP] = st;
         f.state[ST_TAU] = st * f.dt;
     }
-    if (threadIdx.x == 0) parity[blockIdx.x] ^= 1;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        parity[blockIdx.x] ^= 1;
+        left[blockIdx.x] -= 1;
+    }
 }
 
 // plain step counter for non-FEL sims
@@ -348,9 +306,9 @@ cudaError_t launch_fel_finalize(const double *part, int nparts, double *state, d
     return cudaGetLastError();
 }
 
-cudaError_t launch_batch_finalize(const BatchFinal *fin, int ninst, int *parity, cudaStream_t s)
+cudaError_t launch_batch_finalize(const BatchFinal *fin, int ninst, int *parity, int *left, cudaStream_t s)
 {
-    batch_finalize_kernel<<<ninst, kRedThreads, 0, s>>>(fin, parity);
+    batch_finalize_kernel<<<ninst, kRedThreads, 0, s>>>(fin, parity, left);
     return cudaGetLastError();
 }
 

@@ -2,9 +2,14 @@
 //
 // Host code only: a FIFO admission queue, a first-fit allocator over the
 // caller's device arena (the HBM budget), and scheduling rounds that advance
-// every admitted request together through one vp_batch (rebuilt when the set
-// of requests changes; its step is replayed from a CUDA graph) and retire the
-// requests that reached their step count.
+// every admitted request together through one vp_batch. Each round takes a
+// slice of steps; vp_batch_step_each lets every member stop at its own step
+// count inside the slice (its tiles are skipped afterwards), so a nearly
+// finished request does not shorten the others' slice. A request that
+// finishes is retired at once (its moments and kept weights go to the caller)
+// but its simulation stays a member of the batch, taking no steps, until the
+// batch is rebuilt: rebuilds (and their graph capture) happen only when queued
+// requests are admitted, not whenever a member leaves.
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdio.h>
@@ -89,6 +94,7 @@ struct Req {
     double t_submit = 0, t_admit = 0, t_finish = 0;
     bool batched = false;
     bool cancelled = false;   // retire at the start of the next round
+    bool retired = false;     // result handed out; the simulation waits for the next rebuild
 };
 
 }  // namespace
@@ -132,7 +138,7 @@ void drop_batch(vp_server *s)
 
 vp_status admit(vp_server *s)
 {
-    while (!s->queue.empty() && (int)s->active.size() < s->o.max_active) {
+    while (!s->queue.empty() && (int)s->active.size() < s->o.max_active) {   // (after reap)
         Req *q = s->queue.front();
         vp_opts o{q->r.precision, q->r.projection, VP_KERNEL_AUTO, 0, 0, 0, s->o.stream};
         size_t bytes = 0;
@@ -217,31 +223,84 @@ vp_status rebuild_batch(vp_server *s)
     return VP_OK;
 }
 
-// requests cancelled while running leave before the round steps anything
-void retire_cancelled(vp_server *s)
+// Hand out the result of a finished or cancelled request (moments, and the final weights if
+// kept). The simulation itself stays until reap() frees it.
+void retire(vp_server *s, Req *q, bool cancelled)
 {
+    vp_result res{};
+    res.id = q->r.id;
+    res.batched = q->batched ? 1 : 0;
+    res.status = vp_moments(q->sim, &res.moments);
+    if (cancelled && res.status == VP_OK) res.status = VP_ERR_CANCELLED;
+    if (!cancelled && q->r.keep_f && res.status == VP_OK) {
+        const int dt = q->r.precision == VP_FP64 ? VP_FP64 : VP_FP32;
+        const size_t n = (size_t)q->r.grid.nx * q->r.grid.np;
+        std::vector<char> buf(n * (dt == VP_FP64 ? 8 : 4));
+        res.status = vp_get_f(q->sim, buf.data(), dt, n);
+        s->kept_f[q->r.id].swap(buf);
+        s->kept_dtype[q->r.id] = dt;
+    }
+    res.t_submit = q->t_submit;
+    res.t_admit = q->t_admit;
+    res.t_finish = q->t_finish = now_s();
+    s->finished.push_back(res);
+    q->retired = true;
+}
+
+// Free the simulations of retired requests (the batch that holds them goes first).
+void reap(vp_server *s)
+{
+    bool any = false;
+    for (Req *q : s->active) any |= q->retired;
+    if (!any) return;
+    drop_batch(s);
     std::vector<Req *> keep;
     for (Req *q : s->active) {
-        if (!q->cancelled) {
+        if (!q->retired) {
             keep.push_back(q);
             continue;
         }
-        if (s->batch) drop_batch(s);   // a member leaves: the batch is rebuilt
-        vp_result res{};
-        res.id = q->r.id;
-        res.batched = q->batched ? 1 : 0;
-        vp_status st = vp_moments(q->sim, &res.moments);
-        res.status = st == VP_OK ? VP_ERR_CANCELLED : st;
-        res.t_submit = q->t_submit;
-        res.t_admit = q->t_admit;
-        res.t_finish = q->t_finish = now_s();
-        s->finished.push_back(res);
         vp_destroy(q->sim);
         s->alloc.release(q->off, q->bytes);
         delete q;
-        s->dirty = true;
     }
     s->active.swap(keep);
+    s->dirty = true;
+}
+
+// requests cancelled while running leave before the round steps anything
+void retire_cancelled(vp_server *s)
+{
+    for (Req *q : s->active)
+        if (q->cancelled && !q->retired) retire(s, q, true);
+}
+
+int live_count(const vp_server *s)
+{
+    int n = 0;
+    for (const Req *q : s->active) n += q->retired ? 0 : 1;
+    return n;
+}
+
+// Whether freeing the retired members would let the head of the queue in (by the budget and
+// the active limit; an invalid head request is admitted, i.e. failed, at once).
+bool head_would_fit(vp_server *s)
+{
+    if (s->queue.empty()) return false;
+    const Req *q = s->queue.front();
+    size_t freed = 0;
+    int retired = 0;
+    for (const Req *a : s->active)
+        if (a->retired) {
+            freed += align_up(a->bytes);
+            ++retired;
+        }
+    if ((int)s->active.size() - retired >= s->o.max_active) return false;
+    vp_opts o{q->r.precision, q->r.projection, VP_KERNEL_AUTO, 0, 0, 0, s->o.stream};
+    size_t bytes = 0;
+    if (vp_workspace_size(&q->r.grid, q->r.basis, &q->r.pusher, &o, &bytes) != VP_OK) return true;
+    const size_t batch = s->batch ? align_up(s->batch_bytes) : 0;
+    return s->alloc.used() - freed - batch + align_up(bytes) <= s->o.budget_bytes;
 }
 
 }  // namespace
@@ -296,62 +355,41 @@ vp_status vp_server_submit(vp_server *s, const vp_request *req)
 vp_status vp_server_run(vp_server *s, int32_t rounds, int32_t *queued, int32_t *active)
 {
     if (!s) return VP_ERR_ARG;
+    std::vector<int32_t> limits;
     for (int r = 0; r < rounds; ++r) {
         retire_cancelled(s);
-        admit(s);
-        if (s->active.empty()) break;
+        // admission rebuilds the batch: free the retired members first, so that their memory
+        // can take queued requests; with nothing queued they stay and the batch is kept
+        if (live_count(s) == 0 || head_would_fit(s)) {
+            reap(s);
+            admit(s);
+        }
+        if (live_count(s) == 0) {
+            reap(s);
+            break;
+        }
         if (s->dirty) rebuild_batch(s);
-        int slice = s->o.slice_steps;
-        for (Req *q : s->active) slice = std::min(slice, q->r.steps - q->done);
-        if (slice > 0) {
-            if (s->batch) {
-                vp_status st = vp_batch_step(s->batch, slice, 1);
-                if (st != VP_OK)
-                    return sfail(s, st, "batch step: %s", vp_batch_last_error(s->batch));
-            }
+        const int slice = s->o.slice_steps;
+        if (s->batch) {
+            limits.clear();
             for (Req *q : s->active)
-                if (!q->batched) {
-                    vp_status st = vp_step(q->sim, slice);
-                    if (st != VP_OK) return sfail(s, st, "step: %s", vp_last_error(q->sim));
-                }
-            for (Req *q : s->active) q->done += slice;
+                if (q->batched) limits.push_back(q->retired ? 0 : q->r.steps - q->done);
+            vp_status st = vp_batch_step_each(s->batch, slice, limits.data(), 1);
+            if (st != VP_OK) return sfail(s, st, "batch step: %s", vp_batch_last_error(s->batch));
         }
-        // retire finished requests
-        std::vector<Req *> keep;
-        for (Req *q : s->active) {
-            if (q->done < q->r.steps) {
-                keep.push_back(q);
-                continue;
+        for (Req *q : s->active)
+            if (!q->batched && !q->retired) {
+                vp_status st = vp_step(q->sim, std::min(slice, q->r.steps - q->done));
+                if (st != VP_OK) return sfail(s, st, "step: %s", vp_last_error(q->sim));
             }
-            if (s->batch) {
-                drop_batch(s);   // a member leaves: the batch is rebuilt next round
-                s->dirty = true;
-            }
-            vp_result res{};
-            res.id = q->r.id;
-            res.batched = q->batched ? 1 : 0;
-            res.status = vp_moments(q->sim, &res.moments);
-            if (q->r.keep_f && res.status == VP_OK) {
-                const int dt = q->r.precision == VP_FP64 ? VP_FP64 : VP_FP32;
-                const size_t n = (size_t)q->r.grid.nx * q->r.grid.np;
-                std::vector<char> buf(n * (dt == VP_FP64 ? 8 : 4));
-                res.status = vp_get_f(q->sim, buf.data(), dt, n);
-                s->kept_f[q->r.id].swap(buf);
-                s->kept_dtype[q->r.id] = dt;
-            }
-            res.t_submit = q->t_submit;
-            res.t_admit = q->t_admit;
-            res.t_finish = q->t_finish = now_s();
-            s->finished.push_back(res);
-            vp_destroy(q->sim);
-            s->alloc.release(q->off, q->bytes);
-            delete q;
-            s->dirty = true;
-        }
-        s->active.swap(keep);
+        for (Req *q : s->active)
+            if (!q->retired) q->done += std::min(slice, q->r.steps - q->done);
+        // retire requests that reached their step count (their simulations stay until a reap)
+        for (Req *q : s->active)
+            if (!q->retired && q->done >= q->r.steps) retire(s, q, false);
     }
     if (queued) *queued = (int32_t)s->queue.size();
-    if (active) *active = (int32_t)s->active.size();
+    if (active) *active = (int32_t)live_count(s);
     return VP_OK;
 }
 
@@ -372,7 +410,7 @@ vp_status vp_server_cancel(vp_server *s, uint64_t id)
         return VP_OK;
     }
     for (Req *q : s->active)
-        if (q->r.id == id && !q->cancelled) {
+        if (q->r.id == id && !q->cancelled && !q->retired) {
             q->cancelled = true;
             return VP_OK;
         }

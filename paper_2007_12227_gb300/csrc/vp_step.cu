@@ -52,6 +52,10 @@ struct Taps<T, VP_BASIS_SEPTIC_BSPLINE> {
     __device__ __forceinline__ static void weights(T t, T *w) { septic_weights<T>(t, w); }
 };
 
+// FP32 weights rounded to the grid 2^-23 ((x + 1) - 1); FP64 weights as they are
+__device__ __forceinline__ float grid23(float x) { return __fadd_rn(__fadd_rn(x, 1.f), -1.f); }
+__device__ __forceinline__ double grid23(double x) { return x; }
+
 template <typename T>
 struct Taps<T, VP_BASIS_CUBIC_BSPLINE> {
     static constexpr int N = 4;
@@ -62,10 +66,12 @@ struct Taps<T, VP_BASIS_CUBIC_BSPLINE> {
         const T s = T(1) - t;
         const T t2 = t * t, t3 = t2 * t;
         const T sixth = T(1) / T(6);
-        w[0] = s * s * s * sixth;
-        w[3] = t3 * sixth;
-        w[1] = T(2) / T(3) - t2 + T(0.5) * t3;
-        w[2] = (T(1) - (w[0] + w[3])) - w[1];   // partition of unity up to unbiased rounding
+        w[0] = grid23(s * s * s * sixth);
+        w[3] = grid23(t3 * sixth);
+        w[1] = grid23(T(2) / T(3) - t2 + T(0.5) * t3);
+        // partition of unity: in FP32 the three weights above lie on the grid 2^-23, so this
+        // difference is exact and the four sum to exactly one
+        w[2] = ((T(1) - w[0]) - w[3]) - w[1];
     }
 };
 

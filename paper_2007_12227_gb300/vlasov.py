@@ -120,6 +120,7 @@ _SIGNATURES = [
     ("vp_batch_create", C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_void_p, C.c_void_p,
                                   C.c_size_t, C.POINTER(C.c_void_p)]),
     ("vp_batch_step", C.c_int, [C.c_void_p, C.c_int32, C.c_int32]),
+    ("vp_batch_step_each", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.c_int32]),
     ("vp_batch_sync", C.c_int, [C.c_void_p]),
     ("vp_batch_destroy", None, [C.c_void_p]),
     ("vp_batch_last_error", C.c_char_p, [C.c_void_p]),
@@ -331,6 +332,13 @@ class Batch:
 
     def step(self, n=1, use_graph=True):
         st = lib().vp_batch_step(self.h, int(n), 1 if use_graph else 0)
+        if st != VP_OK:
+            raise VlasovError(st, lib().vp_batch_last_error(self.h).decode())
+
+    def step_each(self, n, max_steps, use_graph=True):
+        """n steps; simulation k takes min(n, max_steps[k]) of them."""
+        arr = (C.c_int32 * len(self.sims))(*[int(v) for v in max_steps])
+        st = lib().vp_batch_step_each(self.h, int(n), arr, 1 if use_graph else 0)
         if st != VP_OK:
             raise VlasovError(st, lib().vp_batch_last_error(self.h).decode())
 

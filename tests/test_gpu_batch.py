@@ -119,8 +119,51 @@ def test_batch_tile_shapes_match_oracle(tx):
 def test_batch_autotuned_shapes_match_oracle():
     """Shapes from vp_autotune(batched=1), as the benchmark's batch uses them."""
     wls = [w for w in I.batch_256(count=24, steps=0) if w.grid.nx <= 512][:6]
-    tuned = V.autotune(wls, batched=True)
+    tuned = V.autotune(wls, batched=True, stream=torch.cuda.Stream())
     _batch_vs_oracle(wls, [(r["tile_x"], r["tile_p"]) for r in tuned], 10)
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_batch_step_each_stops_every_simulation_at_its_own_count(use_graph):
+    """vp_batch_step_each: in one call of n steps simulation k takes min(n, max_steps[k]) steps
+    (0 and negative: none) and gives the same bits as stepping it alone that many times; a
+    second call continues from there."""
+    stream = torch.cuda.Stream()
+    wls = mixed_workloads()[:6]
+    batched = make_sims(wls, stream)
+    alone = make_sims(wls, stream)
+    b = V.Batch(batched, stream=stream)
+    first = [9, 0, 4, 12, -3, 9]
+    b.step_each(9, first, use_graph=use_graph)
+    second = [2, 5, 0, 1, 3, 9]
+    b.step_each(5, second, use_graph=use_graph)
+    for k, (wl, sb, sa) in enumerate(zip(wls, batched, alone)):
+        n = max(0, min(9, first[k])) + max(0, min(5, second[k]))
+        if n:
+            sa.step(n)
+        assert sb.moments()["step"] == sa.moments()["step"] == n, wl.name
+        assert np.array_equal(sb.get_f(), sa.get_f()), wl.name
+        if wl.pusher.kind == I.PUSH_FEL:
+            assert np.array_equal(sb.field_history(), sa.field_history()), wl.name
+    b.close()
+
+
+def test_batch_graph_on_the_legacy_stream_steps_directly():
+    """The legacy default stream cannot be captured: use_graph there launches the steps
+    directly and gives the same weights as the graph on a created stream."""
+    wls = [w for w in I.batch_256(count=24, steps=0) if w.grid.nx <= 256][:3]
+    legacy = torch.cuda.default_stream()
+    assert legacy.cuda_stream == 0
+    a = make_sims(wls, legacy)
+    s2 = torch.cuda.Stream()
+    c = make_sims(wls, s2)
+    ba, bc = V.Batch(a, stream=legacy), V.Batch(c, stream=s2)
+    ba.step(5, use_graph=True)
+    bc.step(5, use_graph=True)
+    for x, y in zip(a, c):
+        assert np.array_equal(x.get_f(), y.get_f())
+    ba.close()
+    bc.close()
 
 
 def test_batch_rejects_mixed_precision():
