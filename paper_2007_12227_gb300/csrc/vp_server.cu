@@ -282,6 +282,21 @@ int live_count(const vp_server *s)
     return n;
 }
 
+// Whether the retired members hold most of the batch's nodes: their tiles are skipped in every
+// launch, which costs a work-queue pass per tile; below half the nodes live, rebuild.
+bool mostly_retired(const vp_server *s)
+{
+    if (!s->batch) return false;
+    size_t live = 0, all = 0;
+    for (const Req *q : s->active) {
+        if (!q->batched) continue;
+        const size_t n = (size_t)q->r.grid.nx * q->r.grid.np;
+        all += n;
+        if (!q->retired) live += n;
+    }
+    return all > 0 && 2 * live < all;
+}
+
 // Whether freeing the retired members would let the head of the queue in (by the budget and
 // the active limit; an invalid head request is admitted, i.e. failed, at once).
 bool head_would_fit(vp_server *s)
@@ -360,7 +375,7 @@ vp_status vp_server_run(vp_server *s, int32_t rounds, int32_t *queued, int32_t *
         retire_cancelled(s);
         // admission rebuilds the batch: free the retired members first, so that their memory
         // can take queued requests; with nothing queued they stay and the batch is kept
-        if (live_count(s) == 0 || head_would_fit(s)) {
+        if (live_count(s) == 0 || head_would_fit(s) || mostly_retired(s)) {
             reap(s);
             admit(s);
         }
