@@ -40,6 +40,7 @@ struct Plan {
     // fused kernel: guard band, window stride, threads per CTA, whole-period tiles;
     // state_s: the stored state is s = Lambda_x^{-1} r instead of the weights w
     int G, Gp, ws, threads;
+    int rowcache;   // fused kernel: row-table rows a tile may cache in shared memory
     bool full_row, state_s;
     bool rk4;   // FEL with the RK4 integrator: the scatter kernel and stage reductions
     bool septic_gal;   // cubic B-spline basis, Galerkin: 7-band solves after the scatter deposit
@@ -154,6 +155,7 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     P->full_row = false;
     P->ws = 0;
     P->threads = 0;
+    P->rowcache = 0;
     int ftx = 0, ftp = 0;
     if (kernel == VP_KERNEL_AUTO || kernel == VP_KERNEL_FUSED) {
         const int halo = P->galerkin ? fused_halo(opts->precision) : 0;
@@ -190,6 +192,8 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
             P->full_row = full;
             P->ws = ws;
             P->threads = threads;
+            // the shared memory left beside the window keeps the tile's row table
+            P->rowcache = fused_rowcache_rows(opts->precision, smem, wide ? 1 : 2);
         } else if (kernel == VP_KERNEL_FUSED) {
             return fail(msg, VP_ERR_UNSUPPORTED,
                         "the fused kernel needs a mesh wider than its window (nx = %d)", grid->nx);
@@ -394,6 +398,7 @@ FusedArgs<T> fused_args(vp_sim *s, const void *src, void *dst)
     a.ticket = s->ptr<int>(P.L.ticket);
     a.hist = s->ptr<double>(P.L.hist);
     a.hist_cap = P.hist_cap;
+    a.rowcache = P.rowcache;
     return a;
 }
 
@@ -1105,8 +1110,8 @@ vp_status vp_plan(const vp_sim *s, vp_plan_info *out)
     out->workspace_bytes = (int64_t)P.L.total;
     const bool f64 = P.precision == VP_FP64;
     if (P.kernel == VP_KERNEL_FUSED)
-        out->smem_bytes = (int64_t)(f64 ? fused_smem_bytes<double>(P.ws, P.tp + 2 * P.Gp, P.threads)
-                                        : fused_smem_bytes<float>(P.ws, P.tp + 2 * P.Gp, P.threads));
+        out->smem_bytes = (int64_t)(f64 ? fused_smem_bytes<double>(P.ws, P.tp + 2 * P.Gp, P.threads, P.rowcache)
+                                        : fused_smem_bytes<float>(P.ws, P.tp + 2 * P.Gp, P.threads, P.rowcache));
     else if (P.kernel == VP_KERNEL_TILED)
         out->smem_bytes = (int64_t)(f64 ? tiled_smem_bytes<double>(P.tx, P.tp)
                                         : tiled_smem_bytes<float>(P.tx, P.tp));
@@ -1286,6 +1291,22 @@ vp_status vp_batch_create(vp_sim *const *sims, int32_t count, void *stream, void
         const Plan &P = sims[k]->P;
         b->smem = std::max(b->smem, fused_smem_bytes<float>(P.ws, P.tp + 2 * P.Gp, b->threads));
     }
+    {
+        // every item runs with the batch's thread count: the row cache takes what is left of
+        // the shared memory beside the largest window, if the batch keeps its CTAs per SM
+        const int want = b->threads > kFusedThreads2 ? 1 : 2;
+        int rows = fused_rowcache_rows(VP_FP32, b->smem, want);
+        if (rows > 0 && fused_batch_blocks_per_sm(b->basis, b->projection,
+                                                  b->smem + (size_t)rows * sizeof(RowEntry<float>),
+                                                  b->threads) < want)
+            rows = 0;
+        for (int k = 0; k < count; ++k) {
+            const int r = std::min(rows, sims[k]->P.rowcache);
+            args[2 * k].rowcache = r;
+            args[2 * k + 1].rowcache = r;
+        }
+        b->smem += (size_t)rows * sizeof(RowEntry<float>);
+    }
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
         const Plan &A = sims[a]->P, &C = sims[c]->P;
         return (size_t)A.tx * A.tp > (size_t)C.tx * C.tp;
@@ -1313,7 +1334,7 @@ vp_status vp_batch_create(vp_sim *const *sims, int32_t count, void *stream, void
         return VP_ERR_CUDA;
     }
     // persistent grid: as many CTAs as fit on the device at once
-    per_sm = b->smem > 0 ? (int)std::min<size_t>(2, (size_t)(224 * 1024) / (b->smem + 2048)) : 2;
+    per_sm = std::min(2, fused_batch_blocks_per_sm(b->basis, b->projection, b->smem, b->threads));
     if (per_sm < 1) per_sm = 1;
     b->grid = std::max(1, std::min(nitems, nsm * per_sm));
     e = launch_step_fused_batch<float>(nullptr, nullptr, nullptr, nullptr, 0, nullptr, b->basis, b->projection,

@@ -395,13 +395,15 @@ __device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c)
 // FP32 node: push and tap weights of the x and p axes together in packed pairs. The base
 // cell is round(x - 1/2), so the fraction t lies in [0, 1] (t = 1 at an exact node gives
 // the same deposit as t = 0 one cell further: the B3 and tent kernels are continuous).
-template <int BASIS, bool UTERM>
+// SROW: the row entry lives in shared memory (the tile's row cache), else in global memory
+template <int BASIS, bool UTERM, bool SROW>
 __device__ __forceinline__ void node_taps_f32(const ColC<float> &c, const RowEntry<float> &r,
                                               int colrel, int rowrel, float w, int &m, int &n,
                                               float *wx, float *wy)
 {
-    const float4 q0 = __ldg(reinterpret_cast<const float4 *>(&r));       // ui, vi, uf, vf
-    const float4 q1 = __ldg(reinterpret_cast<const float4 *>(&r) + 1);   // cy, cy, sy, sy
+    const float4 *rq = reinterpret_cast<const float4 *>(&r);
+    const float4 q0 = SROW ? rq[0] : __ldg(rq);       // ui, vi, uf, vf
+    const float4 q1 = SROW ? rq[1] : __ldg(rq + 1);   // cy, cy, sy, sy
     f2_t F = f2_add(f2_pack(c.uf, c.vf), f2_pack(q0.z, q0.w));
     F = f2_fma(f2_pack(UTERM ? c.cu1 : 0.f, c.cv1), f2_pack(q1.x, q1.y), F);
     F = f2_fma(f2_pack(UTERM ? c.cu2 : 0.f, c.cv2), f2_pack(q1.z, q1.w), F);
@@ -444,12 +446,12 @@ __device__ __forceinline__ void node_taps_f32(const ColC<float> &c, const RowEnt
     for (int b = 0; b < TP::N; ++b) wy[b] *= w;
 }
 
-template <typename T, int BASIS, bool UTERM>
+template <typename T, int BASIS, bool UTERM, bool SROW>
 __device__ __forceinline__ void node_taps(const ColC<T> &c, const RowEntry<T> &r, int colrel,
                                           int rowrel, T w, int &m, int &n, T *wx, T *wy)
 {
     if constexpr (sizeof(T) == 4) {
-        node_taps_f32<BASIS, UTERM>(c, r, colrel, rowrel, w, m, n, wx, wy);
+        node_taps_f32<BASIS, UTERM, SROW>(c, r, colrel, rowrel, w, m, n, wx, wy);
         return;
     }
     using TP = FTaps<T, BASIS>;
@@ -724,9 +726,24 @@ __device__ __forceinline__ void gal_rows(T *win, const WinGeom &W, T *dst, int L
             if (sizeof(T) == 4)
 #pragma unroll
                 for (int k = 0; k < KX; ++k) om = fmaxf(om, fabsf((float)v[k]));
-            if (want_part)
+            if (want_part) {
+                // keep s for the column sums: 16-byte stores (lanes 8 words apart: two-way bank
+                // conflicts instead of the eight-way of word stores) when the row start allows
+                if ((reinterpret_cast<uintptr_t>(row) & 15) == 0) {
 #pragma unroll
-                for (int k = 0; k < KX; ++k) row[base + k] = v[k];   // keep s for the column sums
+                    for (int k = 0; k < KX; k += 4) {
+                        float4 q;
+                        q.x = (float)v[k];
+                        q.y = (float)v[k + 1];
+                        q.z = (float)v[k + 2];
+                        q.w = (float)v[k + 3];
+                        *reinterpret_cast<float4 *>(row + base + k) = q;
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < KX; ++k) row[base + k] = v[k];
+                }
+            }
         } else if (!(exact && (base + KX <= D || base >= D + TXe))) {
             // (lanes whose chunk lies in the halo store nothing)
 #pragma unroll
@@ -755,6 +772,8 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
     constexpr int R = (BASIS == VP_BASIS_TENT) ? 1 : 2;
     T *win = reinterpret_cast<T *>(smem_raw);
     T *gcol = win + (size_t)A.ws * (A.tp + 2 * A.Gp);   // [GRows][blockDim] column buffer (Galerkin)
+    // row cache: the tile's rows ja .. jb of the push's row table (when they fit)
+    RowEntry<T> *rowc = reinterpret_cast<RowEntry<T> *>(gcol + (size_t)GRows<T>::value * blockDim.x);
     __shared__ int s_ia, s_ib, s_ja, s_jb, s_smax, s_omax, s_cached;
     __shared__ double s_r4[4][kFusedMaxThreads / 32];
     // Thomas pivots of tridiag(1/6, 2/3, 1/6) in T: entry kPivots holds the limit
@@ -932,6 +951,18 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
         }
     }
 
+    // ---- the row table of the source rows into shared memory, when it fits: every node of a
+    //      row reads that row's entry, and a shared-memory load is shorter than an L1 hit
+    const bool rows_cached = jb >= ja && jb - ja + 1 <= A.rowcache;
+    if (rows_cached) {
+        constexpr int kVec = (int)(sizeof(RowEntry<T>) / 16);
+        const float4 *from = reinterpret_cast<const float4 *>(A.row + ja);
+        float4 *to = reinterpret_cast<float4 *>(rowc);
+        for (int k = tid; k < kVec * (jb - ja + 1); k += blockDim.x) to[k] = __ldg(from + k);
+        __syncthreads();
+    }
+    const RowEntry<T> *srow = rowc - ja;   // srow[j]: row j (rows_cached only)
+
     // ---- walk the source columns
     if (jb >= ja) {
         int wsrc = ib - ia + 1;
@@ -967,11 +998,22 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
             T wx[N], wy[N];
             if (!GAL) {
                 const T *sp = src + (size_t)ja * nx;
+                if (rows_cached) {
 #pragma unroll 2
-                for (int jj = ja; jj <= jb; ++jj, sp += nx) {
-                    int m, n;
-                    node_taps<T, BASIS, UTERM>(cc, A.row[jj], colrel, jj - W.WP0, *sp * qs, m, n, wx, wy);
-                    ring_add<T, N, 1>(win, W, rg, m, n, wx, wy, lost);
+                    for (int jj = ja; jj <= jb; ++jj, sp += nx) {
+                        int m, n;
+                        node_taps<T, BASIS, UTERM, true>(cc, srow[jj], colrel, jj - W.WP0, *sp * qs, m, n, wx,
+                                                         wy);
+                        ring_add<T, N, 1>(win, W, rg, m, n, wx, wy, lost);
+                    }
+                } else {
+#pragma unroll 2
+                    for (int jj = ja; jj <= jb; ++jj, sp += nx) {
+                        int m, n;
+                        node_taps<T, BASIS, UTERM, false>(cc, A.row[jj], colrel, jj - W.WP0, *sp * qs, m, n,
+                                                          wx, wy);
+                        ring_add<T, N, 1>(win, W, rg, m, n, wx, wy, lost);
+                    }
                 }
                 ring_final<T, N>(win, W, rg, lost);
             } else {
@@ -1030,20 +1072,30 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
                             gc[(rr - c_lo) * nth] = gv;
                         }
                     }
-                    const RowEntry<T> *rp = A.row + c_hi;
-                    if (c_lo > kPivots) {
+                    if (c_lo > kPivots && rows_cached) {
+                        const RowEntry<T> *rp = srow + c_hi;
 #pragma unroll 1
                         for (int r = c_hi; r >= c_lo; --r, --rp) {
                             uv = gc[(r - c_lo) * nth] - cp_inf * uv;
                             int m, n;
-                            node_taps<T, BASIS, UTERM>(cc, *rp, colrel, r - W.WP0, uv * qs, m, n, wx, wy);
+                            node_taps<T, BASIS, UTERM, true>(cc, *rp, colrel, r - W.WP0, uv * qs, m, n, wx, wy);
+                            ring_add<T, N, -1>(win, W, rg, m, n, wx, wy, lost);
+                        }
+                    } else if (c_lo > kPivots) {
+                        const RowEntry<T> *rp = A.row + c_hi;
+#pragma unroll 1
+                        for (int r = c_hi; r >= c_lo; --r, --rp) {
+                            uv = gc[(r - c_lo) * nth] - cp_inf * uv;
+                            int m, n;
+                            node_taps<T, BASIS, UTERM, false>(cc, *rp, colrel, r - W.WP0, uv * qs, m, n, wx, wy);
                             ring_add<T, N, -1>(win, W, rg, m, n, wx, wy, lost);
                         }
                     } else {
+                        const RowEntry<T> *rp = A.row + c_hi;
                         for (int r = c_hi; r >= c_lo; --r, --rp) {
                             uv = gc[(r - c_lo) * nth] - piv_cp[min(r, kPivots)] * uv;
                             int m, n;
-                            node_taps<T, BASIS, UTERM>(cc, *rp, colrel, r - W.WP0, uv * qs, m, n, wx, wy);
+                            node_taps<T, BASIS, UTERM, false>(cc, *rp, colrel, r - W.WP0, uv * qs, m, n, wx, wy);
                             ring_add<T, N, -1>(win, W, rg, m, n, wx, wy, lost);
                         }
                     }
@@ -1104,14 +1156,26 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
         // FEL: column sums of w over the tile (Galerkin: sum_j w_ij = sum_j sigma_j s_ij)
         __syncthreads();
         for (int c = tid; c < TXe; c += blockDim.x) {
-            DSum<T> acc;
-            for (int rr = 0; rr < TPe; ++rr) {
-                // Galerkin: the epilogue left s in the own columns; else the cells hold the deposit
-                const T *cell = win + (size_t)(rr + Gp) * W.ws + G + D + c;
-                if (GAL) acc.add_prod(sig_s[rr], *cell);
-                else acc.add(wget(cell, iq));
+            // four interleaved compensated sums (rows rr = q mod 4), added in a fixed order at the
+            // end: four independent chains of shared-memory loads and error-free steps instead of one
+            DSum<T> acc[4];
+            const T *cell = win + (size_t)Gp * W.ws + G + D + c;
+            int rr = 0;
+            for (; rr + 4 <= TPe; rr += 4, cell += 4 * W.ws) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    // Galerkin: the epilogue left s in the own columns; else the cells hold the deposit
+                    if (GAL) acc[q].add_prod(sig_s[rr + q], cell[q * W.ws]);
+                    else acc[q].add(wget(cell + q * W.ws, iq));
+                }
             }
-            const double sum = acc.value();
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                if (rr + q < TPe) {
+                    if (GAL) acc[q].add_prod(sig_s[rr + q], cell[q * W.ws]);
+                    else acc[q].add(wget(cell + q * W.ws, iq));
+                }
+            const double sum = (acc[0].value() + acc[1].value()) + (acc[2].value() + acc[3].value());
             const double2 t = A.csx[X0 + c];
             pw += sum;
             pc += sum * t.x;
@@ -1219,9 +1283,34 @@ __global__ void __launch_bounds__(MINB == 1 ? kFusedMaxThreads : kFusedThreads2,
 }
 
 template <typename T>
-size_t fused_smem_bytes(int ws, int wh, int threads)
+size_t fused_smem_bytes(int ws, int wh, int threads, int rowcache)
 {
-    return (size_t)ws * wh * sizeof(T) + (size_t)GRows<T>::value * threads * sizeof(T);
+    return (size_t)ws * wh * sizeof(T) + (size_t)GRows<T>::value * threads * sizeof(T) +
+           (size_t)rowcache * sizeof(RowEntry<T>);
+}
+
+int fused_rowcache_rows(int precision, size_t base_bytes, int ctas)
+{
+    // shared memory of an SM, reserved per CTA, and the larger static shared memory of the step
+    // kernels (the batched one holds its FusedArgs there); defaults if no device answers
+    int dev = 0, per_sm = 233472, reserved = 1024;
+    size_t stat = 4096;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess) per_sm = v;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrReservedSharedMemoryPerBlock, dev) == cudaSuccess) reserved = v;
+        cudaFuncAttributes fa;
+        const void *k = precision == VP_FP64
+                            ? reinterpret_cast<const void *>(step_fused_batch_kernel<double, VP_BASIS_CUBIC_BSPLINE, true, true, 2>)
+                            : reinterpret_cast<const void *>(step_fused_batch_kernel<float, VP_BASIS_CUBIC_BSPLINE, true, true, 2>);
+        if (cudaFuncGetAttributes(&fa, k) == cudaSuccess) stat = fa.sharedSizeBytes + 256;
+        cudaGetLastError();
+    }
+    const long budget = (long)per_sm / (ctas < 1 ? 1 : ctas) - reserved - (long)stat - (long)base_bytes;
+    const size_t row = precision == VP_FP64 ? sizeof(RowEntry<double>) : sizeof(RowEntry<float>);
+    long rows = budget > 0 ? budget / (long)row : 0;
+    if (rows > 256) rows = 256;
+    return rows >= 32 ? (int)rows : 0;
 }
 
 template <typename T>
@@ -1229,7 +1318,7 @@ cudaError_t launch_step_fused(const FusedArgs<T> &a, int threads, cudaStream_t s
 {
     const int wh = a.tp + 2 * a.Gp;
     // the last CTA's field update uses the window memory as its scratch
-    const size_t smem_tile = fused_smem_bytes<T>(a.ws, wh, threads);
+    const size_t smem_tile = fused_smem_bytes<T>(a.ws, wh, threads, a.rowcache);
     const size_t smem_fin = (size_t)3 * kFinThreads * sizeof(double);
     const size_t smem = smem_tile > smem_fin ? smem_tile : smem_fin;
     const int grid = a.ntx * a.ntp;
@@ -1348,14 +1437,42 @@ cudaError_t launch_step_fused_batch(const FusedArgs<T> *args, const int *parity,
     return cudaGetLastError();
 }
 
+// CTAs of the batched step kernel that fit on one SM with this dynamic shared memory and block
+// size (sets the kernel's shared-memory attribute first); 0 if the query fails
+int fused_batch_blocks_per_sm(int basis, int projection, size_t smem, int threads)
+{
+    const bool gal = basis == VP_BASIS_CUBIC_BSPLINE && projection == VP_PROJ_GALERKIN;
+    const void *k = nullptr;
+    const bool one = threads > kFusedThreads2;
+    if (basis == VP_BASIS_TENT)
+        k = one ? (const void *)step_fused_batch_kernel<float, VP_BASIS_TENT, false, true, 1>
+                : (const void *)step_fused_batch_kernel<float, VP_BASIS_TENT, false, true, 2>;
+    else if (!gal)
+        k = one ? (const void *)step_fused_batch_kernel<float, VP_BASIS_CUBIC_BSPLINE, false, true, 1>
+                : (const void *)step_fused_batch_kernel<float, VP_BASIS_CUBIC_BSPLINE, false, true, 2>;
+    else
+        k = one ? (const void *)step_fused_batch_kernel<float, VP_BASIS_CUBIC_BSPLINE, true, true, 1>
+                : (const void *)step_fused_batch_kernel<float, VP_BASIS_CUBIC_BSPLINE, true, true, 2>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
 template cudaError_t launch_step_fused_batch<float>(const FusedArgs<float> *, const int *, const int *,
                                                     const int2 *, int, int *, int, int, size_t, int,
                                                     int, cudaStream_t);
 template cudaError_t launch_step_fused_batch<double>(const FusedArgs<double> *, const int *, const int *,
                                                      const int2 *, int, int *, int, int, size_t, int,
                                                      int, cudaStream_t);
-template size_t fused_smem_bytes<float>(int, int, int);
-template size_t fused_smem_bytes<double>(int, int, int);
+template size_t fused_smem_bytes<float>(int, int, int, int);
+template size_t fused_smem_bytes<double>(int, int, int, int);
 template cudaError_t launch_step_fused<float>(const FusedArgs<float> &, int, cudaStream_t);
 template cudaError_t launch_step_fused<double>(const FusedArgs<double> &, int, cudaStream_t);
 template cudaError_t launch_lambda_p_mul<float>(const float *, float *, int, int, cudaStream_t);

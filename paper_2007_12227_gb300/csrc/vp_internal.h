@@ -130,6 +130,9 @@ struct FusedArgs {
     int *ticket;
     double *hist;           // FEL field history ring (hist_cap steps)
     int hist_cap;
+    // rows of the push's row table a tile may keep in shared memory (after the window and the
+    // column buffer); a tile whose source rows fit reads them there instead of through L1
+    int rowcache;
 };
 constexpr int kTileSrcUnset = (int)0x80808080;   // the bytes 0x80 (cudaMemset)
 
@@ -182,8 +185,14 @@ size_t tiled_smem_bytes(int tx, int tp);
 
 template <typename T>
 cudaError_t launch_step_fused(const FusedArgs<T> &a, int threads, cudaStream_t s);
+// dynamic shared memory of the one-pass kernel: window (ws x wh), column buffer, row cache
 template <typename T>
-size_t fused_smem_bytes(int ws, int wh, int threads);
+size_t fused_smem_bytes(int ws, int wh, int threads, int rowcache = 0);
+// rows of RowEntry<T> that fit in the shared memory left beside base dynamic bytes, keeping
+// ctas CTAs per SM (0 when fewer than 32 rows fit); queries the current device when it can
+int fused_rowcache_rows(int precision, size_t base_bytes, int ctas);
+// CTAs of the FP32 batched step kernel per SM at this shared memory and block size (0: unknown)
+int fused_batch_blocks_per_sm(int basis, int projection, size_t smem, int threads);
 // left[k]: steps simulation k still takes in this call; its items are skipped at 0
 template <typename T>
 cudaError_t launch_step_fused_batch(const FusedArgs<T> *args, const int *parity, const int *left,
