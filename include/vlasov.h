@@ -238,9 +238,9 @@ const char *vp_status_string(vp_status status);
 /* ---------------------------------------------------------------- batching
  * Many independent simulations (different meshes and pushers, same precision,
  * basis and projection, all on the one-pass kernel) advance together: one
- * persistent launch per step takes (simulation, tile) items from a device work
- * queue, then one launch finishes every simulation's step (FEL field update or
- * step counter). Steady-state steps replay a captured CUDA graph. Each
+ * launch per step runs one CTA per (simulation, tile) item of a device work
+ * list (largest tiles first), then one launch finishes every simulation's step
+ * (FEL field update or step counter). Steady-state steps replay a captured CUDA graph. Each
  * simulation's weights, field and moments stay readable through the vp_sim
  * calls; a simulation must not be stepped on its own while a batch step of it
  * is in flight. The batch keeps its tables in caller-owned device memory. */

@@ -164,7 +164,12 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
         ftx = opts->tile_x ? opts->tile_x : (opts->precision == VP_FP64 ? 128 : 224);
         ftp = opts->tile_p ? opts->tile_p : 64;
         bool full = false;
-        if (grid->nx <= kFusedMaxRow && grid->nx < ftx + 2 * halo + 2 * G + 64) {
+        // whole-period tiles when the mesh is little wider than a windowed tile; by default only
+        // while the tile's source columns fit the two-CTA thread count (a default plan of more
+        // threads runs one CTA per SM, and in a batch it would set that for every item)
+        const bool full_fits = (grid->nx + 2 * R + 8 + 31) / 32 * 32 <= kFusedThreads2;
+        if (grid->nx <= kFusedMaxRow && grid->nx < ftx + 2 * halo + 2 * G + 64 &&
+            (full_fits || opts->tile_x != 0 || grid->nx <= ftx + 2 * halo + 2 * G)) {
             full = true;
             ftx = grid->nx;
         }
@@ -1132,7 +1137,6 @@ struct vp_batch {
     FusedArgs<float> *d_args;
     int *d_parity;
     int2 *d_items;
-    int *d_counter;
     int *d_left;            // per simulation: steps it still takes in the current call
     BatchFinal *d_fin;
     int nitems, ninst, threads, grid, basis, projection;
@@ -1147,7 +1151,7 @@ struct vp_batch {
 namespace {
 
 struct BatchLayout {
-    size_t args, parity, items, counter, left, fin, total;
+    size_t args, parity, items, left, fin, total;
 };
 
 void batch_layout_of(int count, int items, BatchLayout *L);
@@ -1187,7 +1191,6 @@ void batch_layout_of(int count, int items, BatchLayout *L)
     L->args = take(sizeof(FusedArgs<float>) * 2 * count);
     L->parity = take(sizeof(int) * count);
     L->items = take(sizeof(int2) * items);
-    L->counter = take(sizeof(int) * 4);
     L->left = take(sizeof(int) * count);
     L->fin = take(sizeof(BatchFinal) * count);
     L->total = off;
@@ -1202,10 +1205,9 @@ void batch_layout_of(int count, int items, BatchLayout *L)
 
 vp_status batch_enqueue_step(vp_batch *b)
 {
-    VP_BCUDA(b, cudaMemsetAsync(b->d_counter, 0, sizeof(int), b->stream));
     VP_BCUDA(b, launch_step_fused_batch<float>(b->d_args, b->d_parity, b->d_left, b->d_items, b->nitems,
-                                               b->d_counter, b->basis, b->projection, b->smem,
-                                               b->threads, b->grid, b->stream));
+                                               b->basis, b->projection, b->smem, b->threads, b->grid,
+                                               b->stream));
     VP_BCUDA(b, launch_batch_finalize(b->d_fin, b->ninst, b->d_parity, b->d_left, b->stream));
     return VP_OK;
 }
@@ -1255,7 +1257,6 @@ vp_status vp_batch_create(vp_sim *const *sims, int32_t count, void *stream, void
     b->d_args = reinterpret_cast<FusedArgs<float> *>(b->ws + L.args);
     b->d_parity = reinterpret_cast<int *>(b->ws + L.parity);
     b->d_items = reinterpret_cast<int2 *>(b->ws + L.items);
-    b->d_counter = reinterpret_cast<int *>(b->ws + L.counter);
     b->d_left = reinterpret_cast<int *>(b->ws + L.left);
     b->d_fin = reinterpret_cast<BatchFinal *>(b->ws + L.fin);
     b->nitems = nitems;
@@ -1263,7 +1264,7 @@ vp_status vp_batch_create(vp_sim *const *sims, int32_t count, void *stream, void
     b->basis = sims[0]->P.g.basis;
     b->projection = sims[0]->P.g.projection;
     b->have_graph = false;
-    // tables: arguments for both buffer parities, the work queue (largest tiles first), finals
+    // tables: arguments for both buffer parities, the work list (largest tiles first), finals
     std::vector<FusedArgs<float>> args(2 * count);
     std::vector<BatchFinal> fin(count);
     std::vector<int> order(count);
@@ -1316,9 +1317,6 @@ vp_status vp_batch_create(vp_sim *const *sims, int32_t count, void *stream, void
     for (int k : order)
         for (int t = 0; t < sims[k]->P.ntx * sims[k]->P.ntp; ++t) items.push_back(make_int2(k, t));
     cudaError_t e = cudaSuccess;
-    int dev = 0, nsm = 0, per_sm = 0;
-    if (e == cudaSuccess) e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_args, args.data(), sizeof(FusedArgs<float>) * args.size(),
                             cudaMemcpyHostToDevice, b->stream);
@@ -1333,11 +1331,9 @@ vp_status vp_batch_create(vp_sim *const *sims, int32_t count, void *stream, void
         delete b;
         return VP_ERR_CUDA;
     }
-    // persistent grid: as many CTAs as fit on the device at once
-    per_sm = std::min(2, fused_batch_blocks_per_sm(b->basis, b->projection, b->smem, b->threads));
-    if (per_sm < 1) per_sm = 1;
-    b->grid = std::max(1, std::min(nitems, nsm * per_sm));
-    e = launch_step_fused_batch<float>(nullptr, nullptr, nullptr, nullptr, 0, nullptr, b->basis, b->projection,
+    // one CTA per item
+    b->grid = std::max(1, nitems);
+    e = launch_step_fused_batch<float>(nullptr, nullptr, nullptr, nullptr, 0, b->basis, b->projection,
                                        b->smem, b->threads, 0, b->stream);
     if (e != cudaSuccess) {
         delete b;

@@ -1250,36 +1250,28 @@ __global__ void __launch_bounds__(MINB == 1 ? kFusedMaxThreads : kFusedThreads2,
     if (A.ticket) finish_step<T>(A, smem_raw);
 }
 
-// Persistent batched step: CTAs take (instance, tile) items from a counter; instance k
-// uses args[2 k + parity[k]] (parity = which buffer holds its current state).
+// Batched step: CTA b takes the (instance, tile) item b of the work list (largest tiles first;
+// the hardware hands out CTAs in index order as slots free up); instance k uses
+// args[2 k + parity[k]] (parity = which buffer holds its current state) and its tile is skipped
+// once the instance has taken its steps (left[k] == 0). One CTA per item rather than a persistent
+// loop over an atomic counter: inside a loop the compiler kept the arguments of every item live
+// and spilled 400 bytes per thread; one item per CTA spills 60.
 template <typename T, int BASIS, bool GAL, bool UTERM, int MINB>
 __global__ void __launch_bounds__(MINB == 1 ? kFusedMaxThreads : kFusedThreads2, MINB)
     step_fused_batch_kernel(const FusedArgs<T> *__restrict__ args, const int *__restrict__ parity,
-                            const int *__restrict__ left, const int2 *__restrict__ items, int nitems,
-                            int *counter)
+                            const int *__restrict__ left, const int2 *__restrict__ items, int nitems)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(16) FusedArgs<T> sA;
-    __shared__ int s_item;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
-        __syncthreads();
-        const int it = s_item;
-        if (it >= nitems) break;
-        const int2 e = items[it];
-        if (left[e.x] <= 0) {
-            // this simulation takes no more steps in this call: skip its tile
-            __syncthreads();
-            continue;
-        }
-        const FusedArgs<T> *src = args + 2 * e.x + parity[e.x];
-        constexpr int nwords = sizeof(FusedArgs<T>) / 4;
-        for (int k = threadIdx.x; k < nwords; k += blockDim.x)
-            reinterpret_cast<int *>(&sA)[k] = reinterpret_cast<const int *>(src)[k];
-        __syncthreads();
-        fused_tile<T, BASIS, GAL, UTERM>(sA, e.y, smem_raw);
-        __syncthreads();
-    }
+    if ((int)blockIdx.x >= nitems) return;
+    const int2 e = items[blockIdx.x];
+    if (left[e.x] <= 0) return;   // this simulation takes no more steps in this call
+    const FusedArgs<T> *src = args + 2 * e.x + parity[e.x];
+    constexpr int nwords = sizeof(FusedArgs<T>) / 4;
+    for (int k = threadIdx.x; k < nwords; k += blockDim.x)
+        reinterpret_cast<int *>(&sA)[k] = reinterpret_cast<const int *>(src)[k];
+    __syncthreads();
+    fused_tile<T, BASIS, GAL, UTERM>(sA, e.y, smem_raw);
 }
 
 template <typename T>
@@ -1417,8 +1409,8 @@ cudaError_t launch_lambda_p_mul(const T *w, T *s, int nx, int np, cudaStream_t s
 
 template <typename T>
 cudaError_t launch_step_fused_batch(const FusedArgs<T> *args, const int *parity, const int *left,
-                                    const int2 *items, int nitems, int *counter, int basis,
-                                    int projection, size_t smem, int threads, int grid, cudaStream_t s)
+                                    const int2 *items, int nitems, int basis, int projection,
+                                    size_t smem, int threads, int grid, cudaStream_t s)
 {
     const bool gal = basis == VP_BASIS_CUBIC_BSPLINE && projection == VP_PROJ_GALERKIN;
 #define VP_LAUNCH_BATCH(B, GL)                                                                \
@@ -1428,7 +1420,7 @@ cudaError_t launch_step_fused_batch(const FusedArgs<T> *args, const int *parity,
         if (grid <= 0) /* set-up call: shared-memory attribute only (not capturable) */       \
             return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
                                         (int)smem);                                           \
-        k<<<grid, threads, smem, s>>>(args, parity, left, items, nitems, counter);            \
+        k<<<grid, threads, smem, s>>>(args, parity, left, items, nitems);                     \
     } while (0)
     if (basis == VP_BASIS_TENT) VP_LAUNCH_BATCH(VP_BASIS_TENT, false);
     else if (!gal) VP_LAUNCH_BATCH(VP_BASIS_CUBIC_BSPLINE, false);
@@ -1466,11 +1458,11 @@ int fused_batch_blocks_per_sm(int basis, int projection, size_t smem, int thread
 }
 
 template cudaError_t launch_step_fused_batch<float>(const FusedArgs<float> *, const int *, const int *,
-                                                    const int2 *, int, int *, int, int, size_t, int,
-                                                    int, cudaStream_t);
+                                                    const int2 *, int, int, int, size_t, int, int,
+                                                    cudaStream_t);
 template cudaError_t launch_step_fused_batch<double>(const FusedArgs<double> *, const int *, const int *,
-                                                     const int2 *, int, int *, int, int, size_t, int,
-                                                     int, cudaStream_t);
+                                                     const int2 *, int, int, int, size_t, int, int,
+                                                     cudaStream_t);
 template size_t fused_smem_bytes<float>(int, int, int, int);
 template size_t fused_smem_bytes<double>(int, int, int, int);
 template cudaError_t launch_step_fused<float>(const FusedArgs<float> &, int, cudaStream_t);

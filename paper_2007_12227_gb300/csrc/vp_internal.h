@@ -193,11 +193,12 @@ size_t fused_smem_bytes(int ws, int wh, int threads, int rowcache = 0);
 int fused_rowcache_rows(int precision, size_t base_bytes, int ctas);
 // CTAs of the FP32 batched step kernel per SM at this shared memory and block size (0: unknown)
 int fused_batch_blocks_per_sm(int basis, int projection, size_t smem, int threads);
+// one CTA per item (grid >= nitems; grid <= 0: set the shared-memory attribute only);
 // left[k]: steps simulation k still takes in this call; its items are skipped at 0
 template <typename T>
 cudaError_t launch_step_fused_batch(const FusedArgs<T> *args, const int *parity, const int *left,
-                                    const int2 *items, int nitems, int *counter, int basis,
-                                    int projection, size_t smem, int threads, int grid, cudaStream_t s);
+                                    const int2 *items, int nitems, int basis, int projection,
+                                    size_t smem, int threads, int grid, cudaStream_t s);
 
 // per-instance end-of-step work of a batch: FEL field update, or the step counter
 struct BatchFinal {
