@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--serve-count", type=int, default=60,
                     help="requests of the serving trace to run (the whole fixed trace is 2000)")
     ap.add_argument("--tile", default="", help="TX,TP: fixed tile shape instead of the autotuner's")
+    ap.add_argument("--kernel", default="auto", choices=["auto", "fused", "xpass"],
+                    help="step plan: the planner's, the one-pass kernel, or the one-pass tile with a "
+                         "separate x-solve row pass")
     ap.add_argument("--skip-late", action="store_true",
                     help="skip timing the last 20 steps of the workload's run")
     return ap.parse_args()
@@ -407,6 +410,8 @@ def main():
     if dist:
         dist.barrier()
     wl = workload(args.size, args.workload)
+    kernel = {"auto": V.VP_KERNEL_AUTO, "fused": V.VP_KERNEL_FUSED,
+              "xpass": V.VP_KERNEL_FUSED_XPASS}[args.kernel]
     g = wl.grid
     N = g.nodes
     f0 = I.make_f0(wl).astype(np.float32)
@@ -423,9 +428,11 @@ def main():
         tuned = {"tile_x": tx, "tile_p": tp, "candidates": 0, "ms_per_step": None,
                  "default_ms_per_step": None}
     else:
-        tuned = V.autotune([wl], stream=stream)[0]
+        tuned = V.autotune([wl], kernel=kernel, stream=stream)[0]
     t_tune = time.perf_counter() - t_tune
-    sim = V.Sim(g, wl.basis, wl.pusher, precision=V.VP_FP32, tile_x=tuned["tile_x"],
+    # the tuner's plan: its kernel (the one-pass kernel or its separate-x-pass form) and shape
+    plan_kernel = tuned.get("kernel", kernel) if not args.tile else kernel
+    sim = V.Sim(g, wl.basis, wl.pusher, precision=V.VP_FP32, kernel=plan_kernel, tile_x=tuned["tile_x"],
                 tile_p=tuned["tile_p"], stream=stream)
     sim.set_f(f0)
     sim.step(args.warmup)
@@ -475,11 +482,14 @@ def main():
     peak, peak_kind = peaks()
     alg_bytes = bytes_per_node[names[dom]] * N
     achieved = alg_bytes / (phase_ms[dom] * 1e-3) / 1e9
+    xpass = plan["kernel"] == V.VP_KERNEL_FUSED_XPASS
     step_profile = {"pendulum_8192x8192_fp32_cubic": "step_fused_pendulum_8192.md",
                     "fel_4096x2048_fp32_cubic": "step_fused_fel_4096x2048.md"}.get(wl.name, "none.md")
+    if xpass:
+        step_profile = step_profile.replace("step_fused_", "step_fused_xpass_")
     kernel_files = {"push_deposit": (step_profile, FUSED_SOURCES),
-                    "lambda_inv_x": ("filter_x_pendulum_8192.md",
-                                     ["paper_2007_12227_gb300/csrc/vp_filter.cu"]),
+                    "lambda_inv_x": ("xsolve_rows_pendulum_8192.md", FUSED_SOURCES) if xpass else
+                                    ("filter_x_pendulum_8192.md", ["paper_2007_12227_gb300/csrc/vp_filter.cu"]),
                     "lambda_inv_p": ("filter_p_pendulum_8192.md",
                                      ["paper_2007_12227_gb300/csrc/vp_filter.cu"])}
     traffic = None
@@ -585,6 +595,9 @@ def main():
                 "config": {"workload": wl.name, "mesh": f"{g.nx}x{g.np}", "dt": wl.pusher.dt,
                            "basis": "cubic_bspline_galerkin", "parallelism": f"replicas{ws}",
                            "tile": [plan["tile_x"], plan["tile_p"]],
+                           "plan": ("one-pass tile kernel without the x solve + exact x-solve row pass"
+                                    if xpass else "one-pass step kernel"),
+                           "launches_per_step": launches_per_step,
                            "autotune": {"seconds": t_tune, "candidates": tuned["candidates"],
                                         "tuned_ms_per_step": tuned["ms_per_step"],
                                         "default_ms_per_step": tuned["default_ms_per_step"]},

@@ -83,7 +83,12 @@ enum {
     VP_KERNEL_AUTO = 0,     /* planner's choice (fused when the mesh allows, else tiled) */
     VP_KERNEL_TILED = 1,    /* deposit into shared-memory tiles; Lambda^{-1} in two more passes */
     VP_KERNEL_SCATTER = 2,  /* one thread per source node, global atomics (reference path) */
-    VP_KERNEL_FUSED = 3     /* one pass: p solve + push + deposit + x solve per tile */
+    VP_KERNEL_FUSED = 3,    /* one pass: p solve + push + deposit + x solve per tile */
+    /* the one-pass tile without the x solve (no x halo: fewer source columns per tile), then
+     * Lambda_x^{-1} as an exact cyclic pass over whole rows (one more launch, 8 B/node more
+     * traffic). Cubic B-spline Galerkin without the FEL, FP32 rows up to 32768 nodes, FP64 up
+     * to 16384; else VP_ERR_UNSUPPORTED. Not accepted by batches or the server. */
+    VP_KERNEL_FUSED_XPASS = 4
 };
 
 typedef struct vp_grid {
@@ -211,7 +216,7 @@ vp_status vp_moments_static(const void *w, int32_t dtype, const vp_grid *grid,
 
 /* What the planner chose for a simulation (read-only; no device work). */
 typedef struct vp_plan_info {
-    int32_t kernel;           /* VP_KERNEL_FUSED, VP_KERNEL_TILED or VP_KERNEL_SCATTER */
+    int32_t kernel;           /* VP_KERNEL_FUSED, _FUSED_XPASS, _TILED or _SCATTER */
     int32_t tile_x, tile_p;   /* destination tile (fused, tiled); whole mesh for scatter */
     int32_t ntiles_x, ntiles_p;
     int32_t threads;          /* threads per CTA of the fused step kernel, else 0 */
@@ -341,6 +346,10 @@ const char *vp_server_last_error(const vp_server *srv);
  * computes the same step. batched = 1 times the `count` configurations
  * together, each candidate shape applied to all of them as one vp_batch
  * (FP32, one-pass kernel); batched = 0 tunes count = 1 configuration alone.
+ * With batched = 0 and opts->kernel = VP_KERNEL_AUTO, when the planner takes
+ * the one-pass kernel, the separate-x-pass plan (VP_KERNEL_FUSED_XPASS) is
+ * timed over its own shape list too, and the result's kernel says which won:
+ * create the simulation with that kernel and shape.
  * FEL configurations are timed at their A0; the windows grow with |A|.
  * Results are kept in a process-wide cache keyed by the configurations (all
  * grid and pusher fields except A0) and the options, so a second call with

@@ -42,6 +42,10 @@ struct Plan {
     int G, Gp, ws, threads;
     int rowcache;   // fused kernel: row-table rows a tile may cache in shared memory
     bool full_row, state_s;
+    // Galerkin one-pass plan with a separate x pass: tiles without x halo store the deposit into
+    // tmp, and a row pass solves Lambda_x along whole rows into the state buffer
+    bool xpass;
+    int xgrid;   // CTAs of the row pass (persistent)
     bool rk4;   // FEL with the RK4 integrator: the scatter kernel and stage reductions
     bool septic_gal;   // cubic B-spline basis, Galerkin: 7-band solves after the scatter deposit
     double x7_scale;   // septic x solve: the scale that gives the recursions a unit DC gain
@@ -85,7 +89,7 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
         return fail(msg, VP_ERR_ARG, "unknown precision %d", opts->precision);
     if (opts->projection != VP_PROJ_GALERKIN && opts->projection != VP_PROJ_LUMPED)
         return fail(msg, VP_ERR_ARG, "unknown projection %d", opts->projection);
-    if (opts->kernel < 0 || opts->kernel > 3) return fail(msg, VP_ERR_ARG, "unknown kernel %d", opts->kernel);
+    if (opts->kernel < 0 || opts->kernel > 4) return fail(msg, VP_ERR_ARG, "unknown kernel %d", opts->kernel);
     if (opts->tile_x < 0 || opts->tile_p < 0 || opts->history_cap < 0)
         return fail(msg, VP_ERR_ARG, "tile sizes and history capacity must be >= 0");
 
@@ -142,6 +146,21 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     const size_t sz = opts->precision == VP_FP64 ? 8 : 4;
     const bool wide_rotation = pu->kind == VP_PUSH_EXACT_ROTATION && fabs(pu->omega * h) >= 0.5 * M_PI;
     int kernel = opts->kernel;
+    P->xpass = false;
+    if (kernel == VP_KERNEL_FUSED_XPASS) {
+        // the one-pass tile without its x solve, then an exact row pass (cubic B-spline Galerkin;
+        // the FEL's column sums need the solved state inside the tile)
+        if (!P->galerkin || P->fel || P->rk4)
+            return fail(msg, VP_ERR_UNSUPPORTED,
+                        "the separate x pass serves cubic B-spline Galerkin plans without the FEL");
+        int xt = 0, xper = 0;
+        xrow_shape(opts->precision, grid->nx, &xt, &xper);
+        if (xt == 0)
+            return fail(msg, VP_ERR_UNSUPPORTED, "the x-solve row pass takes rows of at most %d nodes",
+                        kXRowMaxThreads * xrow_max_per(opts->precision));
+        P->xpass = true;
+        kernel = VP_KERNEL_FUSED;
+    }
     if (P->rk4 || basis == VP_BASIS_SEPTIC_BSPLINE) {
         // the RK4 end point is not of the tabulated displacement form, and the 8-tap septic
         // deposit has no one-pass form here: global-atomic deposit
@@ -158,7 +177,7 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     P->rowcache = 0;
     int ftx = 0, ftp = 0;
     if (kernel == VP_KERNEL_AUTO || kernel == VP_KERNEL_FUSED) {
-        const int halo = P->galerkin ? fused_halo(opts->precision) : 0;
+        const int halo = P->galerkin && !P->xpass ? fused_halo(opts->precision) : 0;
         const int R = basis == VP_BASIS_TENT ? 1 : 2;
         const int G = P->G, Gp = P->Gp;
         ftx = opts->tile_x ? opts->tile_x : (opts->precision == VP_FP64 ? 128 : 224);
@@ -168,7 +187,7 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
         // while the tile's source columns fit the two-CTA thread count (a default plan of more
         // threads runs one CTA per SM, and in a batch it would set that for every item)
         const bool full_fits = (grid->nx + 2 * R + 8 + 31) / 32 * 32 <= kFusedThreads2;
-        if (grid->nx <= kFusedMaxRow && grid->nx < ftx + 2 * halo + 2 * G + 64 &&
+        if (!P->xpass && grid->nx <= kFusedMaxRow && grid->nx < ftx + 2 * halo + 2 * G + 64 &&
             (full_fits || opts->tile_x != 0 || grid->nx <= ftx + 2 * halo + 2 * G)) {
             full = true;
             ftx = grid->nx;
@@ -234,6 +253,10 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     P->tx = tx;
     P->tp = tp;
     P->ntx = (grid->nx + tx - 1) / tx;
+    if (P->xpass && xrow_smem_bytes(opts->precision, grid->nx, P->ntx) > kMaxSmem)
+        return fail(msg, VP_ERR_UNSUPPORTED, "the x-solve row pass needs %zu bytes of shared memory",
+                    xrow_smem_bytes(opts->precision, grid->nx, P->ntx));
+    P->xgrid = P->xpass ? xrow_grid_size(opts->precision, grid->nx, grid->np, P->ntx) : 0;
     P->ntp = (grid->np + tp - 1) / tp;
     P->hist_cap = opts->history_cap ? opts->history_cap : kDefaultHist;
     P->nlost = (kernel == VP_KERNEL_TILED || kernel == VP_KERNEL_FUSED) ? P->ntx * P->ntp : 1;
@@ -404,6 +427,7 @@ FusedArgs<T> fused_args(vp_sim *s, const void *src, void *dst)
     a.hist = s->ptr<double>(P.L.hist);
     a.hist_cap = P.hist_cap;
     a.rowcache = P.rowcache;
+    a.xpass = P.xpass ? 1 : 0;
     return a;
 }
 
@@ -466,7 +490,9 @@ vp_status do_steps(vp_sim *s, int n, cudaEvent_t *ev = nullptr)
         void *src = s->f(s->cur), *dst = s->f(1 - s->cur);
         StepArgs<T> a = step_args<T>(s, src, dst);
         if (P.kernel == VP_KERNEL_FUSED) {
-            VP_CUDA(s, launch_step_fused<T>(fused_args<T>(s, src, dst), P.threads, s->stream));
+            // separate x pass: the tiles store the deposit into tmp, the row pass solves it into dst
+            void *tile_dst = P.xpass ? static_cast<void *>(s->ptr<T>(P.L.tmp)) : dst;
+            VP_CUDA(s, launch_step_fused<T>(fused_args<T>(s, src, tile_dst), P.threads, s->stream));
         } else if (P.kernel == VP_KERNEL_TILED) {
             VP_CUDA(s, launch_step_tiled<T>(a, s->stream));
         } else {
@@ -485,6 +511,17 @@ vp_status do_steps(vp_sim *s, int n, cudaEvent_t *ev = nullptr)
         int nparts = 0;
         if (P.kernel == VP_KERNEL_FUSED) {
             nparts = P.ntx * P.ntp;
+            if (P.xpass) {
+                float *m0 = s->ptr<float>(P.L.smax);
+                float *mout = P.precision == VP_FP32 ? (src == s->f(0) ? m0 + (size_t)P.ntx * P.ntp : m0) : nullptr;
+                VP_CUDA(s, launch_xsolve_rows<T>(s->ptr<T>(P.L.tmp), static_cast<T *>(dst), P.g.nx, P.g.np,
+                                                 s->ptr<double>(P.L.piv), P.tx, P.tp, P.ntx, mout, err,
+                                                 P.xgrid, s->stream));
+                if (e) {
+                    VP_CUDA(s, cudaEventRecord(e[2], s->stream));
+                    VP_CUDA(s, cudaEventRecord(e[3], s->stream));
+                }
+            }
         } else if (P.galerkin) {
             T *tmp = s->ptr<T>(P.L.tmp);
             VP_CUDA(s, launch_filter_x<T>(static_cast<const T *>(dst), tmp, P.g.nx, P.g.np,
@@ -518,7 +555,7 @@ vp_status do_steps(vp_sim *s, int n, cudaEvent_t *ev = nullptr)
                 nparts = fel_partial_blocks(P.g.nx, P.g.np);
             }
         }
-        if (e && ((!P.galerkin && !P.septic_gal) || P.kernel == VP_KERNEL_FUSED)) {
+        if (e && ((!P.galerkin && !P.septic_gal) || (P.kernel == VP_KERNEL_FUSED && !P.xpass))) {
             VP_CUDA(s, cudaEventRecord(e[2], s->stream));
             VP_CUDA(s, cudaEventRecord(e[3], s->stream));
         }
@@ -1095,7 +1132,7 @@ vp_status vp_plan(const vp_sim *s, vp_plan_info *out)
     if (!s || !out) return VP_ERR_ARG;
     const Plan &P = s->P;
     memset(out, 0, sizeof(*out));
-    out->kernel = P.kernel;
+    out->kernel = P.xpass ? VP_KERNEL_FUSED_XPASS : P.kernel;
     out->tile_x = P.kernel == VP_KERNEL_SCATTER ? P.g.nx : P.tx;
     out->tile_p = P.kernel == VP_KERNEL_SCATTER ? P.g.np : P.tp;
     out->ntiles_x = P.kernel == VP_KERNEL_SCATTER ? 1 : P.ntx;
@@ -1105,7 +1142,7 @@ vp_status vp_plan(const vp_sim *s, vp_plan_info *out)
     out->state_is_s = P.state_s ? 1 : 0;
     // step kernel (+ filters along x and p) (+ FEL partials) + field update or step counter;
     // the one-pass kernel does the field update or the count in its last CTA
-    int n = P.kernel == VP_KERNEL_FUSED ? 1 : 2;
+    int n = P.kernel == VP_KERNEL_FUSED ? (P.xpass ? 2 : 1) : 2;
     if (P.kernel == VP_KERNEL_FUSED && P.fel && P.g.sigma2 != 0.0) n += 2;   // space-charge kick
     if (P.kernel != VP_KERNEL_FUSED && (P.galerkin || P.septic_gal)) n += 2;
     if (P.septic_gal && P.fel) n += 1;   // FEL partial sums after the septic solves
@@ -1165,7 +1202,7 @@ vp_status batch_layout(vp_sim *const *sims, int count, BatchLayout *L, int *nite
         if (!s) return fail(msg, VP_ERR_ARG, "simulation %d is NULL", k);
         const Plan &P = s->P;
         const Plan &P0 = sims[0]->P;
-        if (P.kernel != VP_KERNEL_FUSED)
+        if (P.kernel != VP_KERNEL_FUSED || P.xpass)
             return fail(msg, VP_ERR_UNSUPPORTED, "simulation %d does not use the one-pass kernel", k);
         if (P.precision != VP_FP32)
             return fail(msg, VP_ERR_UNSUPPORTED, "batches hold FP32 simulations (simulation %d)", k);

@@ -787,7 +787,8 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
     const int TXe = min(A.tx, nx - X0), TPe = min(A.tp, np - P0);
     const bool full = A.full_row != 0;
     constexpr int kHalo = Halo<T>::value;
-    const int D = (GAL && !full) ? kHalo : 0;
+    // x halo of the in-tile x solve (none for whole-period tiles and for a separate x pass)
+    const int D = (GAL && !full && !A.xpass) ? kHalo : 0;
     const int G = A.G, Gp = A.Gp;   // guard bands: columns, rows
     WinGeom W;
     W.WW = full ? nx + 2 * G : TXe + 2 * D + 2 * G;
@@ -1131,7 +1132,29 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
     bool bad = false;
     float om = 0.f;   // FP32: max|s'| of the stored outputs
     double pw = 0.0, pc = 0.0, ps = 0.0;
-    if (GAL) {
+    if (GAL && A.xpass) {
+        // separate x pass: store the deposit r = Delta^T w of the own columns in weight units
+        // (one warp per row; 16-byte stores where the row allows); the row pass solves Lambda_x,
+        // records max|s'| per tile and checks the outputs
+        for (int rr = warp; rr < TPe; rr += nwarps) {
+            const T *row = win + (size_t)(rr + Gp) * W.ws + G;
+            T *drow = A.dst + (size_t)(P0 + rr) * nx + X0;
+            int c0 = 0;
+            if constexpr (sizeof(T) == 4) {
+                if ((reinterpret_cast<uintptr_t>(drow) & 15) == 0) {
+                    const int n4 = TXe >> 2;
+                    const int4 *r4 = reinterpret_cast<const int4 *>(row);
+                    float4 *d4 = reinterpret_cast<float4 *>(drow);
+                    for (int c4 = lane; c4 < n4; c4 += 32) {
+                        const int4 q = r4[c4];
+                        d4[c4] = make_float4((float)q.x * iq, (float)q.y * iq, (float)q.z * iq, (float)q.w * iq);
+                    }
+                    c0 = n4 << 2;
+                }
+            }
+            for (int c = c0 + lane; c < TXe; c += 32) drow[c] = wget(row + c, iq);
+        }
+    } else if (GAL) {
         const int L = full ? nx : TXe + 2 * D;
         const bool f32 = sizeof(T) == 4;
         const T sh = f32 ? (T)A.piv[kPivXsFused] : T(-6) * T(-0.26794919243112270647);
@@ -1456,6 +1479,426 @@ int fused_batch_blocks_per_sm(int basis, int projection, size_t smem, int thread
     }
     return n;
 }
+
+// ---------------------------------------------------------------------------
+// Lambda_x^{-1} of whole rows, for plans with a separate x pass (Sec. III: Lambda = Lambda_x (x)
+// Lambda_p, with Lambda_x the cyclic tridiag(1/6, 2/3, 1/6) of the periodic coordinate).
+// Thread t of a row's CTA holds the elements t K .. t K + K - 1 in registers (K = 32 FP32, 16
+// FP64; only the last chunk of a row may be shorter). The causal recurrence y_i = r_i + z y_{i-1}
+// and the anticausal u_i = y_i + z u_{i+1} (z = sqrt(3) - 2) run chunk-locally from zero; a
+// block-wide scan of the pairs (z^len, zero-start end value) gives each chunk its exact carry,
+// and the periodic closure adds z^{i+1} y_{-1} with y_{-1} = E / (1 - z^L), E the zero-start
+// value at L - 1 (anticausal: z^{L-i} u_L with u_L = S / (1 - z^L)), as the whole-period tiles
+// do within a warp. Nothing is truncated. A whole chunk takes its carry and closure as one term,
+// z^{k+1} (carry + z^base y_{-1}), with the powers of z as compile-time constants.
+// The row sits in shared memory with element c at c + V (c / (32 V)), V the elements of 16
+// bytes: the coalesced 16-byte copies and the 16-byte chunk reads of a quarter warp then hit
+// distinct banks. Rows are taken from the last one down: the step kernel wrote the high rows
+// last (still in L2), and the next step reads the low rows first.
+template <typename T>
+__device__ __forceinline__ int xrow_idx(int c)
+{
+    constexpr int V = 16 / (int)sizeof(T), SH = sizeof(T) == 4 ? 5 : 4;
+    return c + V * (c >> SH);
+}
+
+// 16 bytes of shared memory to and from V consecutive register elements
+__device__ __forceinline__ void xload16(const float *p, float *v)
+{
+    const float4 q = *reinterpret_cast<const float4 *>(p);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+}
+__device__ __forceinline__ void xload16(const double *p, double *v)
+{
+    const double2 q = *reinterpret_cast<const double2 *>(p);
+    v[0] = q.x;
+    v[1] = q.y;
+}
+__device__ __forceinline__ void xstore16(float *p, const float *v)
+{
+    *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void xstore16(double *p, const double *v)
+{
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+}
+
+template <typename T>
+__device__ __forceinline__ void xscan_combine(T &A, T &b, T Ao, T bo)
+{
+    // (A, b) after (Ao, bo) along the recurrence: b + A bo, A Ao
+    b = fma(A, bo, b);
+    A *= Ao;
+}
+
+// asynchronous copies from global into shared memory (cp.async): the thread goes on while the
+// copies land in the padded row layout; cp.async.wait_all waits for the thread's own copies
+__device__ __forceinline__ void cp_async_16(void *dst, const void *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+template <int B>
+__device__ __forceinline__ void cp_async_elem(void *dst, const void *src)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// start copying one mesh row into a padded shared-memory row buffer (16-byte copies when every
+// row starts 16-byte aligned, else one element per copy)
+template <typename T>
+__device__ __forceinline__ void xrow_fetch(T *buf, const T *rin, int nx, bool vec)
+{
+    constexpr int V = 16 / (int)sizeof(T);
+    if (vec)
+        for (int q = threadIdx.x; q < nx / V; q += blockDim.x)
+            cp_async_16(buf + xrow_idx<T>(q * V), rin + (size_t)q * V);
+    else
+        for (int c = threadIdx.x; c < nx; c += blockDim.x)
+            cp_async_elem<(int)sizeof(T)>(buf + xrow_idx<T>(c), rin + c);
+    cp_async_commit();
+}
+
+// Block-wide exclusive scan of the chunk pairs (A, b) of one recurrence direction: returns the
+// value the recurrence carries into this thread's chunk, and leaves in sC[nwarps] the value at
+// the row's far end (zero start). DOWN: the anticausal direction (from the last chunk down).
+template <typename T, bool DOWN>
+__device__ __forceinline__ T xrow_carry(T A, T b, T *sA, T *sB, T *sC)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const T Ao = DOWN ? __shfl_down_sync(0xffffffffu, A, off) : __shfl_up_sync(0xffffffffu, A, off);
+        const T bo = DOWN ? __shfl_down_sync(0xffffffffu, b, off) : __shfl_up_sync(0xffffffffu, b, off);
+        if (DOWN ? lane + off < 32 : lane >= off) xscan_combine(A, b, Ao, bo);
+    }
+    __syncthreads();   // the previous scan's sA, sB and sC have been read
+    if (lane == (DOWN ? 0 : 31)) {
+        sA[warp] = A;
+        sB[warp] = b;
+    }
+    T Ae = DOWN ? __shfl_down_sync(0xffffffffu, A, 1) : __shfl_up_sync(0xffffffffu, A, 1);
+    T be = DOWN ? __shfl_down_sync(0xffffffffu, b, 1) : __shfl_up_sync(0xffffffffu, b, 1);
+    if (lane == (DOWN ? 31 : 0)) {
+        Ae = T(1);
+        be = T(0);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        T c = T(0);
+        for (int k = 0; k < nwarps; ++k) {
+            const int w = DOWN ? nwarps - 1 - k : k;
+            sC[w] = c;
+            c = fma(sA[w], c, sB[w]);
+        }
+        sC[nwarps] = c;
+    }
+    __syncthreads();
+    return fma(Ae, sC[warp], be);
+}
+
+// Lambda_x^{-1} (times -1/(6z)) of one row whose elements base .. base + len - 1 this thread
+// holds in v (len == K: a whole chunk), the threads of the block holding the row in order.
+template <typename T, int K>
+__device__ __forceinline__ void xsolve_row_regs(T *v, const int base, const int len, const int nx,
+                                                T *sA, T *sB, T *sC)
+{
+    const int nwarps = blockDim.x >> 5;
+    const T z = (T)zconst(1);
+    const bool whole = len == K;
+    // causal sweep from zero, then the carry and the periodic closure
+    T y = T(0), A = T(1);
+    if (whole) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            y = fma(z, y, v[k]);
+            v[k] = y;
+        }
+        A = (T)zconst(K);
+    } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (k < len) {
+                y = fma(z, y, v[k]);
+                v[k] = y;
+                A *= z;
+            }
+    }
+    {
+        const T carry = xrow_carry<T, false>(A, y, sA, sB, sC);
+        const T yprev = sC[nwarps] / (T(1) - zpow<T>(nx));   // y_{-1} = y_{L-1}
+        const T cin = fma(zpow<T>(base), yprev, carry);     // element base + k: z^{k+1} cin
+        if (whole) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] = fma((T)zconst(k + 1), cin, v[k]);
+        } else {
+            T zk = z;
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (k < len) {
+                    v[k] = fma(zk, cin, v[k]);
+                    zk *= z;
+                }
+        }
+    }
+    // anticausal sweep from zero at the chunk end, then the carry and the periodic closure
+    T u = T(0);
+    A = T(1);
+    if (whole) {
+#pragma unroll
+        for (int k = K - 1; k >= 0; --k) {
+            u = fma(z, u, v[k]);
+            v[k] = u;
+        }
+        A = (T)zconst(K);
+    } else {
+#pragma unroll
+        for (int k = K - 1; k >= 0; --k)
+            if (k < len) {
+                u = fma(z, u, v[k]);
+                v[k] = u;
+                A *= z;
+            }
+    }
+    {
+        const T carry = xrow_carry<T, true>(A, u, sA, sB, sC);
+        const T unext = sC[nwarps] / (T(1) - zpow<T>(nx));   // u_L = u_0
+        // element base + k: z^{len - k} (carry + z^{L - base - len} u_L)
+        const T cin = len > 0 ? fma(zpow<T>(nx - base - len), unext, carry) : T(0);
+        if (whole) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) v[k] = fma((T)zconst(K - k), cin, v[k]);
+        } else {
+            T zk = z;
+#pragma unroll
+            for (int k = K - 1; k >= 0; --k)
+                if (k < len) {
+                    v[k] = fma(zk, cin, v[k]);
+                    zk *= z;
+                }
+        }
+    }
+}
+
+// Persistent: each CTA takes rows np - 1 - blockIdx.x, then gridDim.x further down, and copies
+// the next row into its second buffer while it solves the current one.
+template <typename T, int K, int MAXT>
+__global__ void __launch_bounds__(MAXT)
+    xsolve_rows_kernel(const T *__restrict__ r, T *__restrict__ out, int nx, int np,
+                       const double *__restrict__ piv, int tx, int tp, int ntx,
+                       float *__restrict__ smax_out, unsigned *__restrict__ err, int row_stride, int nbuf)
+{
+    extern __shared__ __align__(16) unsigned char xs_raw[];
+    T *buf0 = reinterpret_cast<T *>(xs_raw);
+    int *tmax = reinterpret_cast<int *>(buf0 + (size_t)nbuf * row_stride);
+    __shared__ T sA[MAXT / 32], sB[MAXT / 32], sC[MAXT / 32 + 1];
+    constexpr int V = 16 / (int)sizeof(T);
+    const int tid = threadIdx.x;
+    const bool vec = (nx % V) == 0;   // every row starts 16-byte aligned
+    const T sh = sizeof(T) == 4 ? (T)piv[kPivXsFused] : T(-6) * (T)zconst(1);
+    const T sl = sizeof(T) == 4 ? (T)piv[kPivXsFused + 1] : T(0);
+    const int base = tid * K;
+    const int len = max(0, min(K, nx - base));
+    // a chunk lies in one tile when the tile width is a multiple of the chunk
+    const bool one_tile = tx % K == 0;
+
+    // zeros past the row end in every buffer (read with the last chunks, never stored)
+    for (int b = 0; b < nbuf; ++b)
+        for (int c = nx + tid; c < (int)blockDim.x * K; c += blockDim.x)
+            buf0[(size_t)b * row_stride + xrow_idx<T>(c)] = T(0);
+    if (sizeof(T) == 4)
+        for (int k = tid; k < ntx; k += blockDim.x) tmax[k] = 0;
+    int i = blockIdx.x;
+    if (i < np) xrow_fetch(buf0, r + (size_t)(np - 1 - i) * nx, nx, vec);
+    bool bad = false;
+    for (int it = 0; i < np; i += gridDim.x, ++it) {
+        const int row = np - 1 - i;
+        T *cur = buf0 + (size_t)(nbuf == 2 ? (it & 1) : 0) * row_stride;
+        cp_async_wait_all();
+        __syncthreads();   // the row is in cur; the stores of the other buffer's row have read it
+        const int inext = i + gridDim.x;
+        if (nbuf == 2 && inext < np)
+            xrow_fetch(buf0 + (size_t)((it + 1) & 1) * row_stride, r + (size_t)(np - 1 - inext) * nx, nx, vec);
+
+        T v[K];
+#pragma unroll
+        for (int j = 0; j < K / V; ++j) xload16(cur + xrow_idx<T>(base + j * V), &v[j * V]);
+        xsolve_row_regs<T, K>(v, base, len, nx, sA, sB, sC);
+
+        // the scale -6z (FP32: the step's unit-DC-gain pair sh + sl), checks, per-tile max|s'|
+        T chk = T(0);
+        float m = 0.f;
+        if (len == K) {
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                v[k] = sizeof(T) == 4 ? fma(v[k], sl, v[k] * sh) : v[k] * sh;
+                chk = fma(v[k], T(0), chk);
+                m = fmaxf(m, fabsf((float)v[k]));
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (k < len) {
+                    v[k] = sizeof(T) == 4 ? fma(v[k], sl, v[k] * sh) : v[k] * sh;
+                    chk = fma(v[k], T(0), chk);
+                    m = fmaxf(m, fabsf((float)v[k]));
+                }
+        }
+        bad |= chk != T(0);
+        if (sizeof(T) == 4 && len > 0) {
+            if (one_tile) {
+                if (m > 0.f) atomicMax(&tmax[base / tx], __float_as_int(m));
+            } else {
+                int tc = base / tx, nb = (tc + 1) * tx;
+                m = 0.f;
+#pragma unroll
+                for (int k = 0; k < K; ++k)
+                    if (k < len) {
+                        if (base + k >= nb) {
+                            if (m > 0.f) atomicMax(&tmax[tc], __float_as_int(m));
+                            m = 0.f;
+                            ++tc;
+                            nb += tx;
+                        }
+                        m = fmaxf(m, fabsf((float)v[k]));
+                    }
+                if (m > 0.f) atomicMax(&tmax[tc], __float_as_int(m));
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < K / V; ++j) xstore16(cur + xrow_idx<T>(base + j * V), &v[j * V]);
+        __syncthreads();
+
+        T *rout = out + (size_t)row * nx;
+        if (vec) {
+            int4 *o4 = reinterpret_cast<int4 *>(rout);
+            for (int q = tid; q < nx / V; q += blockDim.x)
+                o4[q] = *reinterpret_cast<const int4 *>(cur + xrow_idx<T>(q * V));
+        } else {
+            for (int c = tid; c < nx; c += blockDim.x) rout[c] = cur[xrow_idx<T>(c)];
+        }
+        if (sizeof(T) == 4) {
+            int *mo = reinterpret_cast<int *>(smax_out) + (size_t)(row / tp) * ntx;
+            for (int k = tid; k < ntx; k += blockDim.x) {
+                const int mk = tmax[k];
+                if (mk != 0) {
+                    atomicMax(mo + k, mk);
+                    tmax[k] = 0;
+                }
+            }
+        }
+        if (nbuf == 1 && inext < np) {
+            __syncthreads();
+            xrow_fetch(cur, r + (size_t)(np - 1 - inext) * nx, nx, vec);
+        }
+    }
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(err, ERRF_NONFINITE);
+}
+
+void xrow_shape(int precision, int nx, int *threads, int *per)
+{
+    const int K = xrow_max_per(precision);
+    *threads = 0;
+    *per = 0;
+    if (nx < 1 || (long)nx > (long)kXRowMaxThreads * K) return;
+    *threads = ((nx + K - 1) / K + 31) / 32 * 32;
+    *per = K;
+}
+
+// bytes of one padded row buffer (a multiple of 16): every chunk of every thread, with the pads
+static size_t xrow_row_bytes(int precision, int nx)
+{
+    int t = 0, p = 0;
+    xrow_shape(precision, nx, &t, &p);
+    if (t == 0) return 0;
+    const int V = precision == VP_FP64 ? 2 : 4, line = precision == VP_FP64 ? 16 : 32;
+    const size_t sz = precision == VP_FP64 ? 8 : 4;
+    const size_t n = (size_t)t * p;
+    return ((n + V * (n / line) + V) * sz + 15) & ~(size_t)15;
+}
+
+// two row buffers (the next row is copied in while the current one is solved) when they fit
+int xrow_buffers(int precision, int nx, int ntx)
+{
+    const size_t tm = precision == VP_FP64 ? 0 : (size_t)ntx * sizeof(int);
+    return 2 * xrow_row_bytes(precision, nx) + tm <= (size_t)200 * 1024 ? 2 : 1;
+}
+
+size_t xrow_smem_bytes(int precision, int nx, int ntx)
+{
+    const size_t row = xrow_row_bytes(precision, nx);
+    if (row == 0) return 0;
+    return (size_t)xrow_buffers(precision, nx, ntx) * row +
+           (precision == VP_FP64 ? 0 : (size_t)ntx * sizeof(int));
+}
+
+// block-size bound of the instantiation: rows up to 256 chunks (FP32 8192 nodes) keep their
+// chunks in registers at two CTAs per SM; the larger forms serve longer rows
+template <typename T>
+static auto xrow_kernel(int threads)
+{
+    constexpr int K = sizeof(T) == 8 ? 16 : 32;
+    return threads <= 256 ? xsolve_rows_kernel<T, K, 256>
+                          : (threads <= 512 ? xsolve_rows_kernel<T, K, 512> : xsolve_rows_kernel<T, K, 1024>);
+}
+
+template <typename T>
+static int xrow_grid_of(int nx, int np, int ntx)
+{
+    const int prec = sizeof(T) == 8 ? VP_FP64 : VP_FP32;
+    int threads = 0, per = 0;
+    xrow_shape(prec, nx, &threads, &per);
+    if (threads == 0) return 0;
+    const size_t smem = xrow_smem_bytes(prec, nx, ntx);
+    auto k = xrow_kernel<T>(threads);
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return np;   // one CTA per row
+    }
+    const long g = (long)sms * (per_sm > 0 ? per_sm : 1);
+    return (int)(g < np ? g : np);
+}
+
+int xrow_grid_size(int precision, int nx, int np, int ntx)
+{
+    return precision == VP_FP64 ? xrow_grid_of<double>(nx, np, ntx) : xrow_grid_of<float>(nx, np, ntx);
+}
+
+template <typename T>
+cudaError_t launch_xsolve_rows(const T *r, T *out, int nx, int np, const double *piv, int tx, int tp,
+                               int ntx, float *smax_out, unsigned *err, int grid, cudaStream_t s)
+{
+    const int prec = sizeof(T) == 8 ? VP_FP64 : VP_FP32;
+    int threads = 0, per = 0;
+    xrow_shape(prec, nx, &threads, &per);
+    if (threads == 0) return cudaErrorInvalidValue;
+    const size_t smem = xrow_smem_bytes(prec, nx, ntx);
+    const int nbuf = xrow_buffers(prec, nx, ntx);
+    const int stride = (int)(xrow_row_bytes(prec, nx) / sizeof(T));
+    auto k = xrow_kernel<T>(threads);
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (grid <= 0 || grid > np) grid = np;
+    k<<<grid, threads, smem, s>>>(r, out, nx, np, piv, tx, tp, ntx, smax_out, err, stride, nbuf);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_xsolve_rows<float>(const float *, float *, int, int, const double *, int, int,
+                                               int, float *, unsigned *, int, cudaStream_t);
+template cudaError_t launch_xsolve_rows<double>(const double *, double *, int, int, const double *, int,
+                                                int, int, float *, unsigned *, int, cudaStream_t);
 
 template cudaError_t launch_step_fused_batch<float>(const FusedArgs<float> *, const int *, const int *,
                                                     const int2 *, int, int, int, size_t, int, int,

@@ -133,6 +133,9 @@ struct FusedArgs {
     // rows of the push's row table a tile may keep in shared memory (after the window and the
     // column buffer); a tile whose source rows fit reads them there instead of through L1
     int rowcache;
+    // Galerkin plans with a separate x pass: the tile stores its deposit r = Delta^T w (own
+    // columns, no x halo) and xsolve_rows_kernel applies Lambda_x^{-1} to whole rows afterwards
+    int xpass;
 };
 constexpr int kTileSrcUnset = (int)0x80808080;   // the bytes 0x80 (cudaMemset)
 
@@ -213,6 +216,23 @@ cudaError_t launch_batch_finalize(const BatchFinal *fin, int ninst, int *parity,
 // device bytes of a batch of `count` simulations with `items` tiles in all
 size_t batch_workspace_bytes(int count, int items);
 constexpr int fused_halo(int precision) { return precision == VP_FP64 ? 28 : 16; }
+// the x-solve row pass of plans with a separate x pass: one CTA per mesh row, each thread a
+// contiguous chunk of at most kXRowMaxPer elements (FP32 32, FP64 16)
+constexpr int kXRowMaxThreads = 1024;
+constexpr int xrow_max_per(int precision) { return precision == VP_FP64 ? 16 : 32; }
+// threads and chunk length for rows of nx (0 threads: nx too long for the pass)
+void xrow_shape(int precision, int nx, int *threads, int *per);
+size_t xrow_smem_bytes(int precision, int nx, int ntx);
+// row buffers of the pass (2: the next row is copied in while one is solved) and its grid (a
+// persistent CTA count from the occupancy of the current device, at most np)
+int xrow_buffers(int precision, int nx, int ntx);
+int xrow_grid_size(int precision, int nx, int np, int ntx);
+// s' = Lambda_x^{-1} r along every row (cyclic, exact: block-wide carries, no truncation), then
+// FP32: the per-tile max|s'| into smax_out[ntp][ntx] (atomic max over the zeros the step kernel
+// stored); non-finite outputs set ERRF_NONFINITE
+template <typename T>
+cudaError_t launch_xsolve_rows(const T *r, T *out, int nx, int np, const double *piv, int tx, int tp,
+                               int ntx, float *smax_out, unsigned *err, int grid, cudaStream_t s);
 constexpr int kFusedMaxRow = 512; // longest window row one warp solves
 constexpr int kFusedMaxTileP = 256; // tallest tile of the fused kernel
 template <typename T>

@@ -33,12 +33,15 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Shape {
     int tx, tp;
+    int kernel;   // -1: the caller's opts.kernel
 };
 
-// the planner's default first, then widths x heights; batched runs use a shorter list
-std::vector<Shape> candidate_shapes(int precision, bool batched)
+// the planner's default first, then widths x heights; batched runs use a shorter list. xpass:
+// also the one-pass tiles with a separate x pass (no x halo, so a tile of width w walks about
+// w + 12 source columns: widths up to 288 keep two CTAs per SM)
+std::vector<Shape> candidate_shapes(int precision, bool batched, bool xpass = false)
 {
-    std::vector<Shape> c{{0, 0}};
+    std::vector<Shape> c{{0, 0, -1}};
     static const int w32[] = {96, 128, 160, 192, 224, 256, 320, 384, 448};
     // heights include multiples of the warp counts of the common widths (60 = 6 x 10, 63 = 9 x 7),
     // which give each warp of the x solve the same number of window rows; which height wins
@@ -48,15 +51,29 @@ std::vector<Shape> candidate_shapes(int precision, bool batched)
     static const int h64[] = {16, 32, 64};
     static const int wb[] = {128, 160, 224, 320};
     static const int hb[] = {16, 32, 63, 64};
+    static const int wx32[] = {128, 192, 224, 256, 288};
+    static const int hx32[] = {32, 60, 63, 64, 128};
+    static const int wx64[] = {64, 96, 128, 192, 256};
+    static const int hx64[] = {16, 32, 64};
     if (batched) {
         for (int w : wb)
-            for (int h : hb) c.push_back({w, h});
+            for (int h : hb) c.push_back({w, h, -1});
     } else if (precision == VP_FP64) {
         for (int w : w64)
-            for (int h : h64) c.push_back({w, h});
+            for (int h : h64) c.push_back({w, h, -1});
     } else {
         for (int w : w32)
-            for (int h : h32) c.push_back({w, h});
+            for (int h : h32) c.push_back({w, h, -1});
+    }
+    if (xpass && !batched) {
+        c.push_back({0, 0, VP_KERNEL_FUSED_XPASS});
+        if (precision == VP_FP64) {
+            for (int w : wx64)
+                for (int h : hx64) c.push_back({w, h, VP_KERNEL_FUSED_XPASS});
+        } else {
+            for (int w : wx32)
+                for (int h : hx32) c.push_back({w, h, VP_KERNEL_FUSED_XPASS});
+        }
     }
     return c;
 }
@@ -89,6 +106,10 @@ std::string cache_key(const vp_tune_config *cfgs, int count, const vp_opts *o, c
 }
 
 size_t nodes_of(const vp_grid &g) { return (size_t)g.nx * (size_t)g.np; }
+
+// a single configuration tuned for the planner's choice also times the separate-x-pass plan
+// (batches take the one-pass kernel only)
+bool tunes_xpass(const vp_opts *o, const vp_tune_opts &t) { return !t.batched && o->kernel == VP_KERNEL_AUTO; }
 
 // Device time of one step: warm-up, then the better of two runs of k steps, k grown until a run
 // lasts min_ms.
@@ -137,7 +158,7 @@ struct Need {
 vp_status workspace_need(const vp_tune_config *cfgs, int count, const vp_opts *opts,
                          const vp_tune_opts &t, Need *need)
 {
-    const std::vector<Shape> shapes = candidate_shapes(opts->precision, t.batched != 0);
+    const std::vector<Shape> shapes = candidate_shapes(opts->precision, t.batched != 0, tunes_xpass(opts, t));
     const size_t sz = opts->precision == VP_FP64 ? 8 : 4;
     need->sim.assign(count, 0);
     size_t off = 0, maxn = 0;
@@ -148,6 +169,7 @@ vp_status workspace_need(const vp_tune_config *cfgs, int count, const vp_opts *o
             vp_opts o = *opts;
             o.tile_x = s.tx;
             o.tile_p = s.tp;
+            if (s.kernel >= 0) o.kernel = s.kernel;
             size_t b = 0;
             if (vp_workspace_size(&c.grid, c.basis, &c.pusher, &o, &b) == VP_OK)
                 need->sim[i] = std::max(need->sim[i], b);
@@ -246,13 +268,13 @@ vp_status vp_autotune(const vp_tune_config *cfgs, int32_t count, const vp_opts *
             return VP_ERR_CUDA;
     }
 
-    const std::vector<Shape> shapes = candidate_shapes(opts->precision, t.batched != 0);
+    const std::vector<Shape> shapes = candidate_shapes(opts->precision, t.batched != 0, tunes_xpass(opts, t));
     std::set<std::vector<int>> seen;
     std::vector<vp_tune_result> best(count);
     double best_ms = INFINITY, default_ms = NAN;
     int timed = 0, default_kernel = -1;
     for (const Shape &shape : shapes) {
-        const bool is_default = shape.tx == 0 && shape.tp == 0;
+        const bool is_default = shape.tx == 0 && shape.tp == 0 && shape.kernel < 0;
         std::vector<vp_sim *> sims;
         std::vector<vp_plan_info> info;
         bool ok = true;
@@ -260,6 +282,7 @@ vp_status vp_autotune(const vp_tune_config *cfgs, int32_t count, const vp_opts *
             vp_opts o = *opts;
             o.tile_x = shape.tx;
             o.tile_p = shape.tp;
+            if (shape.kernel >= 0) o.kernel = shape.kernel;
             vp_sim *s = nullptr;
             const size_t cap = t.batched ? need.sim[i] : need.sim[0];
             if (vp_create(&cfgs[i].grid, cfgs[i].basis, &cfgs[i].pusher, &o, sim_ws[i], cap, &s) != VP_OK) {
@@ -273,10 +296,14 @@ vp_status vp_autotune(const vp_tune_config *cfgs, int32_t count, const vp_opts *
             if (t.batched && pi.kernel != VP_KERNEL_FUSED) ok = false;
         }
         if (ok && is_default) default_kernel = info[0].kernel;
-        // only shapes of the default plan's kernel compete
-        if (ok && !t.batched && info[0].kernel != default_kernel) ok = false;
+        // only shapes of the default plan's kernel compete (and, next to the one-pass kernel, its
+        // separate-x-pass form)
+        if (ok && !t.batched && info[0].kernel != default_kernel &&
+            !(default_kernel == VP_KERNEL_FUSED && info[0].kernel == VP_KERNEL_FUSED_XPASS))
+            ok = false;
         std::vector<int> sig;
         for (const vp_plan_info &pi : info) {
+            sig.push_back(pi.kernel);
             sig.push_back(pi.tile_x);
             sig.push_back(pi.tile_p);
             sig.push_back(pi.threads);

@@ -22,7 +22,7 @@ VP_PUSH_LEAPFROG_KDK, VP_PUSH_EXACT_ROTATION, VP_PUSH_FEL_DKD, VP_PUSH_FEL_RK4 =
 VP_POT_FREE, VP_POT_PENDULUM, VP_POT_HARMONIC = 0, 1, 2
 VP_FP32, VP_FP64 = 0, 1
 VP_PROJ_GALERKIN, VP_PROJ_LUMPED = 0, 1
-VP_KERNEL_AUTO, VP_KERNEL_TILED, VP_KERNEL_SCATTER, VP_KERNEL_FUSED = 0, 1, 2, 3
+VP_KERNEL_AUTO, VP_KERNEL_TILED, VP_KERNEL_SCATTER, VP_KERNEL_FUSED, VP_KERNEL_FUSED_XPASS = 0, 1, 2, 3, 4
 
 
 class vp_grid(C.Structure):

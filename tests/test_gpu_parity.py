@@ -322,9 +322,9 @@ def test_pendulum_8192_fp32_cubic_at_bench_tiles(tile, steps):
 
 
 def test_pendulum_8192_fp32_cubic_at_the_autotuned_tile():
-    """Exactly the plan the benchmark's headline line uses: the shape the autotuner picks on
-    this device for the 8192^2 pendulum, one step against the oracle."""
+    """Exactly the plan the benchmark's headline line uses: the kernel and shape the autotuner
+    picks on this device for the 8192^2 pendulum, two steps against the oracle."""
     wl = I.pendulum_8192_fp32_cubic()
     tuned = V.autotune([wl])[0]
-    got, st, _, _, _ = run_pair(wl, 1, tile=(tuned["tile_x"], tuned["tile_p"]))
+    got, st, _, _, _ = run_pair(wl, 2, kernel=tuned["kernel"], tile=(tuned["tile_x"], tuned["tile_p"]))
     check(got, st.w, I.FP32)
