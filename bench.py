@@ -135,14 +135,14 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def traffic_from_profile(kernel_file, source_files, tile=None):
-    """Per-launch DRAM bytes from the committed ncu summary, if the kernel is unchanged and the
-    summary was taken with the same tile shape."""
+def traffic_from_profile(kernel_file, source_files, tile=None, key="traffic_bytes_per_launch"):
+    """Per-launch DRAM bytes (or another per-launch figure, by key) from the committed ncu summary,
+    if the kernel is unchanged and the summary was taken with the same tile shape."""
     path = os.path.join(ROOT, "profiles", kernel_file)
     if not os.path.exists(path):
         return None
     text = open(path).read()
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m = re.search(key + r":\s*([0-9.eE+]+)", text)
     h = re.search(r"source_sha256:\s*([0-9a-f]{64})", text)
     if not m or not h:
         return None
@@ -492,11 +492,11 @@ def main():
                                     ("filter_x_pendulum_8192.md", ["paper_2007_12227_gb300/csrc/vp_filter.cu"]),
                     "lambda_inv_p": ("filter_p_pendulum_8192.md",
                                      ["paper_2007_12227_gb300/csrc/vp_filter.cu"])}
-    traffic = None
+    traffic = inst = None
     if names[dom] in kernel_files:
-        traffic = traffic_from_profile(*kernel_files[names[dom]],
-                                       tile=(plan["tile_x"], plan["tile_p"]) if names[dom] == "push_deposit"
-                                       else None)
+        ptile = (plan["tile_x"], plan["tile_p"]) if names[dom] == "push_deposit" else None
+        traffic = traffic_from_profile(*kernel_files[names[dom]], tile=ptile)
+        inst = traffic_from_profile(*kernel_files[names[dom]], tile=ptile, key="inst_executed_per_launch")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": names[dom],
                 "peak_source": f"{peak_kind} hbm_gbs",
@@ -504,6 +504,18 @@ def main():
                 "phase_ms": dict(zip(names, phase_ms)),
                 "step_algorithmic_gbs": 8 * N / (ms_per_step * 1e-3) / 1e9,
                 "step_frac": 8 * N / (ms_per_step * 1e-3) / 1e9 / peak}
+    # instruction-issue roofline of the same kernel: warp instructions per launch (committed ncu
+    # count, same source and tile) over its live time, against 4 issue slots per SM and cycle at the
+    # median SM clock sampled during the timed region
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = (clocks or {}).get("sm_mhz") or (clocks or {}).get("sm_max_mhz")
+    if inst and mhz:
+        issue_peak = sms * 4 * mhz * 1e6
+        issue_rate = inst / (phase_ms[dom] * 1e-3)
+        roofline["issue"] = {"inst_per_launch": inst, "unit": "warp instructions/s",
+                             "achieved": issue_rate, "peak": issue_peak, "frac": issue_rate / issue_peak,
+                             "thread_inst_per_node": inst * 32 / N, "sms": sms, "sm_mhz": mhz,
+                             "source": "ncu smsp__inst_executed.sum of the committed profile"}
 
     # ---- late in the run: the last 20 of the workload's 2000 steps (the state filaments, the
     #      kernel's work depends on it), timed the same way outside the headline region

@@ -1566,10 +1566,11 @@ __device__ __forceinline__ void xrow_fetch(T *buf, const T *rin, int nx, bool ve
 }
 
 // Block-wide exclusive scan of the chunk pairs (A, b) of one recurrence direction: returns the
-// value the recurrence carries into this thread's chunk, and leaves in sC[nwarps] the value at
-// the row's far end (zero start). DOWN: the anticausal direction (from the last chunk down).
+// value the recurrence carries into this thread's chunk, and in total the value at the row's far
+// end (zero start). DOWN: the anticausal direction (from the last chunk down). One barrier: every
+// warp combines the per-warp totals itself; each direction has its own sA, sB.
 template <typename T, bool DOWN>
-__device__ __forceinline__ T xrow_carry(T A, T b, T *sA, T *sB, T *sC)
+__device__ __forceinline__ T xrow_carry(T A, T b, T *sA, T *sB, T &total)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
 #pragma unroll
@@ -1578,7 +1579,6 @@ __device__ __forceinline__ T xrow_carry(T A, T b, T *sA, T *sB, T *sC)
         const T bo = DOWN ? __shfl_down_sync(0xffffffffu, b, off) : __shfl_up_sync(0xffffffffu, b, off);
         if (DOWN ? lane + off < 32 : lane >= off) xscan_combine(A, b, Ao, bo);
     }
-    __syncthreads();   // the previous scan's sA, sB and sC have been read
     if (lane == (DOWN ? 0 : 31)) {
         sA[warp] = A;
         sB[warp] = b;
@@ -1590,26 +1590,24 @@ __device__ __forceinline__ T xrow_carry(T A, T b, T *sA, T *sB, T *sC)
         be = T(0);
     }
     __syncthreads();
-    if (tid == 0) {
-        T c = T(0);
-        for (int k = 0; k < nwarps; ++k) {
-            const int w = DOWN ? nwarps - 1 - k : k;
-            sC[w] = c;
-            c = fma(sA[w], c, sB[w]);
-        }
-        sC[nwarps] = c;
+    T c = T(0), cw = T(0);
+    for (int k = 0; k < nwarps; ++k) {
+        const int w = DOWN ? nwarps - 1 - k : k;
+        if (w == warp) cw = c;
+        c = fma(sA[w], c, sB[w]);
     }
-    __syncthreads();
-    return fma(Ae, sC[warp], be);
+    total = c;
+    return fma(Ae, cw, be);
 }
 
 // Lambda_x^{-1} (times -1/(6z)) of one row whose elements base .. base + len - 1 this thread
 // holds in v (len == K: a whole chunk), the threads of the block holding the row in order.
+// sA, sB: [2][warps], one pair of arrays per direction (a row's causal scan and the next row's
+// are separated by the anticausal scan's barrier and the row's store barrier).
 template <typename T, int K>
 __device__ __forceinline__ void xsolve_row_regs(T *v, const int base, const int len, const int nx,
-                                                T *sA, T *sB, T *sC)
+                                                T (*sA)[kXRowMaxThreads / 32], T (*sB)[kXRowMaxThreads / 32])
 {
-    const int nwarps = blockDim.x >> 5;
     const T z = (T)zconst(1);
     const bool whole = len == K;
     // causal sweep from zero, then the carry and the periodic closure
@@ -1631,8 +1629,9 @@ __device__ __forceinline__ void xsolve_row_regs(T *v, const int base, const int 
             }
     }
     {
-        const T carry = xrow_carry<T, false>(A, y, sA, sB, sC);
-        const T yprev = sC[nwarps] / (T(1) - zpow<T>(nx));   // y_{-1} = y_{L-1}
+        T E;
+        const T carry = xrow_carry<T, false>(A, y, sA[0], sB[0], E);
+        const T yprev = E / (T(1) - zpow<T>(nx));   // y_{-1} = y_{L-1}
         const T cin = fma(zpow<T>(base), yprev, carry);     // element base + k: z^{k+1} cin
         if (whole) {
 #pragma unroll
@@ -1667,8 +1666,9 @@ __device__ __forceinline__ void xsolve_row_regs(T *v, const int base, const int 
             }
     }
     {
-        const T carry = xrow_carry<T, true>(A, u, sA, sB, sC);
-        const T unext = sC[nwarps] / (T(1) - zpow<T>(nx));   // u_L = u_0
+        T S;
+        const T carry = xrow_carry<T, true>(A, u, sA[1], sB[1], S);
+        const T unext = S / (T(1) - zpow<T>(nx));   // u_L = u_0
         // element base + k: z^{len - k} (carry + z^{L - base - len} u_L)
         const T cin = len > 0 ? fma(zpow<T>(nx - base - len), unext, carry) : T(0);
         if (whole) {
@@ -1689,7 +1689,7 @@ __device__ __forceinline__ void xsolve_row_regs(T *v, const int base, const int 
 // Persistent: each CTA takes rows np - 1 - blockIdx.x, then gridDim.x further down, and copies
 // the next row into its second buffer while it solves the current one.
 template <typename T, int K, int MAXT>
-__global__ void __launch_bounds__(MAXT)
+__global__ void __launch_bounds__(MAXT, MAXT == 256 ? 3 : 1)
     xsolve_rows_kernel(const T *__restrict__ r, T *__restrict__ out, int nx, int np,
                        const double *__restrict__ piv, int tx, int tp, int ntx,
                        float *__restrict__ smax_out, unsigned *__restrict__ err, int row_stride, int nbuf)
@@ -1697,7 +1697,7 @@ __global__ void __launch_bounds__(MAXT)
     extern __shared__ __align__(16) unsigned char xs_raw[];
     T *buf0 = reinterpret_cast<T *>(xs_raw);
     int *tmax = reinterpret_cast<int *>(buf0 + (size_t)nbuf * row_stride);
-    __shared__ T sA[MAXT / 32], sB[MAXT / 32], sC[MAXT / 32 + 1];
+    __shared__ T sA[2][kXRowMaxThreads / 32], sB[2][kXRowMaxThreads / 32];
     constexpr int V = 16 / (int)sizeof(T);
     const int tid = threadIdx.x;
     const bool vec = (nx % V) == 0;   // every row starts 16-byte aligned
@@ -1729,7 +1729,7 @@ __global__ void __launch_bounds__(MAXT)
         T v[K];
 #pragma unroll
         for (int j = 0; j < K / V; ++j) xload16(cur + xrow_idx<T>(base + j * V), &v[j * V]);
-        xsolve_row_regs<T, K>(v, base, len, nx, sA, sB, sC);
+        xsolve_row_regs<T, K>(v, base, len, nx, sA, sB);
 
         // the scale -6z (FP32: the step's unit-DC-gain pair sh + sl), checks, per-tile max|s'|
         T chk = T(0);
