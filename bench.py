@@ -561,7 +561,10 @@ def main():
     extra = {}
     if not args.skip_extra and rank == 0:
         fel = I.fel_4096x2048_fp32_cubic()
-        fsim = V.Sim(fel.grid, fel.basis, fel.pusher, precision=V.VP_FP32, stream=stream)
+        # the autotuner's plan (kernel and tile shape), as for the headline workload
+        ftuned = V.autotune([fel], stream=stream)[0]
+        fsim = V.Sim(fel.grid, fel.basis, fel.pusher, precision=V.VP_FP32, kernel=ftuned["kernel"],
+                     tile_x=ftuned["tile_x"], tile_p=ftuned["tile_p"], stream=stream)
         fsim.set_f(I.make_f0(fel).astype(np.float32))
         fsim.step(20)
         fsim.sync()
@@ -577,8 +580,11 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         warm = e0.elapsed_time(e1) / nf
+        fplan = fsim.plan()
         extra[fel.name] = {"node_updates_per_s": fel.grid.nodes / (fms * 1e-3),
                            "ms_per_step": fms, "steps_timed": nf,
+                           "tile": [fplan["tile_x"], fplan["tile_p"]],
+                           "plan": "separate x pass" if fplan["kernel"] == V.VP_KERNEL_FUSED_XPASS else "one pass",
                            "l2": "flushed before every timed step",
                            "phase_ms": dict(zip(names, [p / nf for p in fph])),
                            "warm_l2_ms_per_step": warm}

@@ -86,8 +86,10 @@ enum {
     VP_KERNEL_FUSED = 3,    /* one pass: p solve + push + deposit + x solve per tile */
     /* the one-pass tile without the x solve (no x halo: fewer source columns per tile), then
      * Lambda_x^{-1} as an exact cyclic pass over whole rows (one more launch, 8 B/node more
-     * traffic). Cubic B-spline Galerkin without the FEL, FP32 rows up to 32768 nodes, FP64 up
-     * to 16384; else VP_ERR_UNSUPPORTED. Not accepted by batches or the server. */
+     * traffic). Cubic B-spline Galerkin (the FEL's bunching is summed from the deposit and
+     * divided by the eigenvalue 2/3 + cos(h_theta)/3 of Lambda_x at exp(-i theta)); not the RK4
+     * FEL; FP32 rows up to 32768 nodes, FP64 up to 16384; else VP_ERR_UNSUPPORTED. Not accepted
+     * by batches or the server. */
     VP_KERNEL_FUSED_XPASS = 4
 };
 

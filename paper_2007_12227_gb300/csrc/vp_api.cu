@@ -149,10 +149,10 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     P->xpass = false;
     if (kernel == VP_KERNEL_FUSED_XPASS) {
         // the one-pass tile without its x solve, then an exact row pass (cubic B-spline Galerkin;
-        // the FEL's column sums need the solved state inside the tile)
-        if (!P->galerkin || P->fel || P->rk4)
+        // the FEL's bunching sums come from the deposit through the eigenvalue of Lambda_x)
+        if (!P->galerkin || P->rk4)
             return fail(msg, VP_ERR_UNSUPPORTED,
-                        "the separate x pass serves cubic B-spline Galerkin plans without the FEL");
+                        "the separate x pass serves cubic B-spline Galerkin plans (not the RK4 FEL)");
         int xt = 0, xper = 0;
         xrow_shape(opts->precision, grid->nx, &xt, &xper);
         if (xt == 0)
@@ -428,6 +428,7 @@ FusedArgs<T> fused_args(vp_sim *s, const void *src, void *dst)
     a.hist_cap = P.hist_cap;
     a.rowcache = P.rowcache;
     a.xpass = P.xpass ? 1 : 0;
+    a.bunch_x = P.xpass && P.fel ? 1.0 / (2.0 / 3.0 + cos(P.g.hx) / 3.0) : 1.0;
     return a;
 }
 

@@ -1176,8 +1176,11 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
         }
     }
     if (want_part) {
-        // FEL: column sums of w over the tile (Galerkin: sum_j w_ij = sum_j sigma_j s_ij)
+        // FEL: column sums of w over the tile (Galerkin: sum_j w_ij = sum_j sigma_j s_ij; with a
+        // separate x pass the window keeps the deposit r, and bunch_x turns its cos/sin sums into
+        // those of s')
         __syncthreads();
+        const bool sums_of_s = GAL && !A.xpass;
         for (int c = tid; c < TXe; c += blockDim.x) {
             // four interleaved compensated sums (rows rr = q mod 4), added in a fixed order at the
             // end: four independent chains of shared-memory loads and error-free steps instead of one
@@ -1187,16 +1190,19 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
             for (; rr + 4 <= TPe; rr += 4, cell += 4 * W.ws) {
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    // Galerkin: the epilogue left s in the own columns; else the cells hold the deposit
-                    if (GAL) acc[q].add_prod(sig_s[rr + q], cell[q * W.ws]);
-                    else acc[q].add(wget(cell + q * W.ws, iq));
+                    // in-tile x solve: the epilogue left s in the own columns; else the cells hold
+                    // the deposit
+                    const T v = sums_of_s ? cell[q * W.ws] : wget(cell + q * W.ws, iq);
+                    if (GAL) acc[q].add_prod(sig_s[rr + q], v);
+                    else acc[q].add(v);
                 }
             }
 #pragma unroll
             for (int q = 0; q < 3; ++q)
                 if (rr + q < TPe) {
-                    if (GAL) acc[q].add_prod(sig_s[rr + q], cell[q * W.ws]);
-                    else acc[q].add(wget(cell + q * W.ws, iq));
+                    const T v = sums_of_s ? cell[q * W.ws] : wget(cell + q * W.ws, iq);
+                    if (GAL) acc[q].add_prod(sig_s[rr + q], v);
+                    else acc[q].add(v);
                 }
             const double sum = (acc[0].value() + acc[1].value()) + (acc[2].value() + acc[3].value());
             const double2 t = A.csx[X0 + c];
@@ -1204,6 +1210,8 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
             pc += sum * t.x;
             ps += sum * t.y;
         }
+        pc *= A.bunch_x;
+        ps *= A.bunch_x;
     }
     if (bad) atomicOr(A.err, ERRF_NONFINITE);
 
@@ -1213,7 +1221,8 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
     const bool reduce = __syncthreads_or(lost != 0.0 || want_part);
     if (sizeof(T) == 4 && tid == 0) A.smax_out[tile] = __int_as_float(s_omax);
     if (!reduce) return;
-    double vals[4] = {qs > T(0) ? lost / (double)qs : 0.0, pw, pc, ps};
+    // lost weight back to weight units: iq = 1 / qs exactly (a power of two; 0 for a dropped deposit)
+    double vals[4] = {lost * (double)iq, pw, pc, ps};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         double v = vals[q];

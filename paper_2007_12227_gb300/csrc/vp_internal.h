@@ -136,6 +136,11 @@ struct FusedArgs {
     // Galerkin plans with a separate x pass: the tile stores its deposit r = Delta^T w (own
     // columns, no x halo) and xsolve_rows_kernel applies Lambda_x^{-1} to whole rows afterwards
     int xpass;
+    // FEL with a separate x pass: the tile sums the deposit r instead of s' = Lambda_x^{-1} r. The
+    // circulant Lambda_x has the mode exp(-i theta) as an eigenvector (eigenvalue
+    // lambda_1 = 2/3 + cos(h_theta)/3; the constant mode: 1), so the cos/sin sums of s' are those of r
+    // times bunch_x = 1 / lambda_1 (1 when the tile solves x itself)
+    double bunch_x;
 };
 constexpr int kTileSrcUnset = (int)0x80808080;   // the bytes 0x80 (cudaMemset)
 

@@ -137,12 +137,95 @@ def test_xpass_is_deterministic():
     assert np.array_equal(a, b)
 
 
+def fel(nth, np_, precision, dt=0.05, a0=0.05, sp=0.1, pr=(-1.0, 1.0), sigma2=0.0, kind=None):
+    return I.Workload("t", I.Grid(nth, np_, 0.0, 2 * PI, *pr),
+                      I.Pusher(kind if kind is not None else I.PUSH_FEL, I.POT_FREE, 1.0, 1.0, dt, a0, 0.0,
+                               0.0, sigma2),
+                      I.BASIS_CUBIC, precision, 0, "fel_gaussian", dict(sp=sp, eps=1e-4))
+
+
+def run_fel(wl, steps, kernel=XP, tile=(0, 0)):
+    f0 = I.make_f0(wl)
+    sim = V.Sim(wl.grid, wl.basis, wl.pusher, precision=wl.precision, kernel=kernel,
+                tile_x=tile[0], tile_p=tile[1])
+    plan = sim.plan()
+    sim.set_f(f0 if wl.precision == I.FP64 else f0.astype(np.float32))
+    sim.step(steps)
+    got, hist = sim.get_f(), sim.field_history()
+    sim.close()
+    st = O.State(wl.grid, wl.pusher, wl.basis, I.PROJ_GALERKIN,
+                 f0 if wl.precision == I.FP64 else f0.astype(np.float32).astype(np.float64))
+    ohist = st.run(steps, history=True)
+    return got, hist, st, ohist, plan
+
+
+# Against the oracle these FP64 FEL meshes (640 and 700 theta points) run 8 steps: the oracle
+# pushes absolute phases, whose rounding (up to (nx / 2) eps cells per node and step) reaches the
+# 1e-12 bound over longer runs on meshes this fine (as for the one-pass kernel in
+# test_gpu_fel_full). The longer run compares the two GPU plans with each other.
+@pytest.mark.parametrize("shape,tile", [((640, 96), (0, 0)), ((700, 130), (96, 48))])
+def test_xpass_fel_fp64_field_history(shape, tile):
+    """FEL with the separate x pass: the tile's bunching sums come from the deposit r, divided by
+    the eigenvalue of Lambda_x at exp(-i theta); f and the field history must match the oracle's
+    (which sums the weights themselves) to the FP64 bound."""
+    wl = fel(shape[0], shape[1], I.FP64)
+    got, hist, st, ohist, plan = run_fel(wl, 8, tile=tile)
+    assert plan["kernel"] == XP
+    assert rel_linf(got, st.w) <= FP64_TOL
+    amp = np.max(np.hypot(ohist[:, 0], ohist[:, 1]))
+    assert np.max(np.abs(hist - ohist)) <= FP64_TOL * amp
+
+
+@pytest.mark.parametrize("sigma2", [0.0, 0.3])
+def test_xpass_fel_fp64_matches_one_pass_over_30_steps(sigma2):
+    """30 steps: the separate-x-pass plan and the one-pass kernel give the same f and field (the
+    in-tile solve truncates at |z|^28; the bunching identity holds to rounding). sigma2 != 0: the
+    space-charge kick reads the stored state the row pass wrote."""
+    wl = fel(640, 96, I.FP64, sigma2=sigma2)
+    f0 = I.make_f0(wl)
+    out = []
+    for kernel in (V.VP_KERNEL_FUSED, XP):
+        sim = V.Sim(wl.grid, wl.basis, wl.pusher, precision=I.FP64, kernel=kernel)
+        sim.set_f(f0)
+        sim.step(30)
+        out.append((sim.get_f(), sim.field_history()))
+        sim.close()
+    (fa, ha), (fb, hb) = out
+    assert rel_linf(fb, fa) <= 1e-13
+    assert np.max(np.abs(hb - ha)) <= 1e-13 * np.max(np.hypot(ha[:, 0], ha[:, 1]))
+
+
+def test_xpass_fel_fp64_space_charge():
+    """sigma^2 != 0 against the oracle."""
+    wl = fel(640, 96, I.FP64, sigma2=0.3)
+    got, hist, st, ohist, _ = run_fel(wl, 8)
+    assert rel_linf(got, st.w) <= FP64_TOL
+    amp = np.max(np.hypot(ohist[:, 0], ohist[:, 1]))
+    assert np.max(np.abs(hist - ohist)) <= FP64_TOL * amp
+
+
+def test_xpass_fel_fp32_reduced_grid():
+    """The 4096 x 2048 FEL workload's physics (sigma_p 0.05) on 1024 x 512, 60 steps: f within
+    the FP32 bound, |A| within the FP32 field bound of the parity tests (5e-4)."""
+    wl = fel(1024, 512, I.FP32, dt=0.01, a0=0.05, sp=0.05, pr=(-0.8, 0.8))
+    got, hist, st, ohist, _ = run_fel(wl, 60)
+    assert rel_l1(got, st.w) <= FP32_TOL
+    amp = np.hypot(ohist[:, 0], ohist[:, 1])
+    assert np.max(np.abs(np.hypot(hist[:, 0], hist[:, 1]) - amp) / amp) <= 5e-4
+
+
+def test_xpass_fel_4096x2048_full_size():
+    wl = I.fel_4096x2048_fp32_cubic()
+    got, hist, st, ohist, plan = run_fel(wl, 3)
+    assert plan["kernel"] == XP
+    assert rel_l1(got, st.w) <= FP32_TOL
+    assert np.max(np.abs(hist - ohist)) <= 1e-6 * np.max(np.hypot(ohist[:, 0], ohist[:, 1]))
+
+
 def test_xpass_unsupported_plans():
-    fel = I.Workload("t", I.Grid(512, 128, 0.0, 2 * PI, -1.0, 1.0),
-                     I.Pusher(I.PUSH_FEL, I.POT_FREE, 1.0, 1.0, 0.01, 1e-3, 0.0), I.BASIS_CUBIC, I.FP32,
-                     0, "fel_gaussian", dict(sp=0.05, eps=1e-4))
+    rk4 = fel(512, 128, I.FP32, kind=I.PUSH_FEL_RK4)
     tent = pend(512, 128, I.FP32)
-    for wl, kw in ((fel, {}), (tent, dict(projection=I.PROJ_LUMPED))):
+    for wl, kw in ((rk4, {}), (tent, dict(projection=I.PROJ_LUMPED))):
         with pytest.raises(V.VlasovError) as ei:
             V.Sim(wl.grid, wl.basis, wl.pusher, precision=I.FP32, kernel=XP, **kw)
         assert ei.value.status == V.VP_ERR_UNSUPPORTED
