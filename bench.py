@@ -4,7 +4,9 @@
 Default workload: pendulum H = p^2/2 - cos x on an 8192 x 8192 mesh, FP32
 weights, cubic B-spline deposit with the Galerkin mass-matrix solve
 (tent basis), leapfrog dt = 0.02; one benchmark step = one vp_step(1):
-push + deposit + Lambda^{-1} (x and p solves) + step bookkeeping.
+push + deposit + Lambda^{-1} (x and p solves) + step bookkeeping, on the plan
+the library's autotuner picks (the one-pass kernel, or its tile pass without
+the x solve followed by the x-solve row pass).
 
 Prints one JSON line. value = node-updates/s over all ranks (each rank runs
 an independent replica: the step has no cross-GPU exchange at this size).

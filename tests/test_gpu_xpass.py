@@ -76,8 +76,10 @@ def test_xpass_fp64_ragged_tiles(shape, tile):
     assert e <= FP64_TOL, f"rel Linf {e:.3e}"
 
 
-@pytest.mark.parametrize("tile", [(224, 64), (480, 32), (96, 128), (224, 63)])
+@pytest.mark.parametrize("tile", [(224, 64), (480, 32), (96, 128), (224, 63), (200, 48), (100, 64)])
 def test_xpass_fp32_windowed_tiles(tile):
+    """Widths 200 and 100 are not multiples of the row pass's 32-node chunks: chunks that cross a
+    tile boundary record their per-tile maxima (the next step's window scale) piece by piece."""
     wl = pend(1100, 700, I.FP32, dt=0.02, pr=(-4.0, 4.0), pc=0.5, s=0.4)
     got, mom, _ = run(wl, 25, tile=tile)
     st = oracle(wl, 25)
