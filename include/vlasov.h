@@ -234,8 +234,9 @@ vp_status vp_plan(const vp_sim *sim, vp_plan_info *out);
 /* Redirect later work to another stream (no synchronisation is implied). */
 vp_status vp_set_stream(vp_sim *sim, void *stream);
 
-/* Device pointer of the current weights (valid until the next vp_step), for reading:
- * change the state only through vp_set_f / vp_set_f_device. */
+/* Device pointer of the current weights (valid until the next vp_step or vp_set_f), for
+ * reading: change the state only through vp_set_f / vp_set_f_device. With the stored state
+ * s = Lambda_p w the weights are computed into the buffer the next step writes. */
 vp_status vp_state_device(vp_sim *sim, void **dev);
 
 void vp_destroy(vp_sim *sim);

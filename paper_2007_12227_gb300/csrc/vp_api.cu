@@ -277,7 +277,10 @@ vp_status make_plan(const vp_grid *grid, int32_t basis, const vp_pusher *pu, con
     };
     L.f0 = take(N * sz);
     L.f1 = take(N * sz);
-    L.tmp = take(P->galerkin || P->septic_gal ? N * sz : 0);
+    // a third mesh-sized buffer only where a step needs one: the deposit between the two launches of
+    // the separate-x-pass plan, the x-solve output of the separate-filter path. The one-pass plan
+    // reads its weights out through the idle ping-pong buffer instead
+    L.tmp = take(((P->galerkin && (kernel != VP_KERNEL_FUSED || P->xpass)) || P->septic_gal) ? N * sz : 0);
     L.col = take(grid->nx * colsz);
     L.row = take(grid->np * rowsz);
     L.rowb = take(grid->np * sizeof(RowBound));
@@ -432,7 +435,8 @@ FusedArgs<T> fused_args(vp_sim *s, const void *src, void *dst)
     return a;
 }
 
-// the weights w of the current state: the state itself, or Lambda_p^{-1} s in scratch
+// the weights w of the current state: the state itself, or Lambda_p^{-1} s into out, else into the
+// idle ping-pong buffer (the next step's output: it overwrites them)
 template <typename T>
 vp_status weights_of_state(vp_sim *s, const void **w, void *out = nullptr)
 {
@@ -441,7 +445,7 @@ vp_status weights_of_state(vp_sim *s, const void **w, void *out = nullptr)
         *w = s->f(s->cur);
         return VP_OK;
     }
-    T *tmp = out ? static_cast<T *>(out) : s->ptr<T>(P.L.tmp);
+    T *tmp = out ? static_cast<T *>(out) : static_cast<T *>(s->f(1 - s->cur));
     VP_CUDA(s, launch_filter_p<T>(static_cast<const T *>(s->f(s->cur)), tmp, P.g.nx, P.g.np,
                                   s->ptr<double>(P.L.piv), s->ptr<double2>(P.L.csx),
                                   s->ptr<double>(P.L.part), 0, s->ptr<unsigned>(P.L.err), s->stream));
@@ -857,8 +861,8 @@ static vp_status set_f_common(vp_sim *s, const void *src, int32_t dtype, size_t 
     if (!src || n != N || (dtype != VP_FP32 && dtype != VP_FP64))
         return fail(s->msg, VP_ERR_ARG, "set_f: need %zu values of dtype FP32/FP64", N);
     s->cur = 0;
-    // the weights go to the state buffer, or to scratch when the state is s = Lambda_p w
-    void *dst = P.state_s ? (void *)(s->ws + P.L.tmp) : s->f(0);
+    // the weights go to the state buffer, or to the idle buffer f1 when the state is s = Lambda_p w
+    void *dst = P.state_s ? s->f(1) : s->f(0);
     const size_t szs = P.precision == VP_FP64 ? 8 : 4;
     // pinned host weights and the state s = Lambda_p w: Lambda_p reads them in place
     void *hdev = (!device && dtype == P.precision && P.state_s) ? host_device_ptr(src, szs) : nullptr;

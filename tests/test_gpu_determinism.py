@@ -63,3 +63,25 @@ def test_batch_equals_alone_bitwise():
     b.close()
     for s in batched:
         s.close()
+
+
+@pytest.mark.parametrize("wl", [I.pendulum_8192_fp32_cubic(1024, 512),
+                                I.fel_4096x2048_fp32_cubic(512, 256)])
+def test_reading_the_weights_between_steps_changes_nothing(wl):
+    """With the stored state s = Lambda_p w, vp_get_f, vp_moments and vp_state_device compute w
+    into the idle ping-pong buffer, which the next step overwrites: reading between steps must
+    leave every later step's bits as they are."""
+    f_plain, h_plain = run(wl, 12)
+    sim = V.Sim(wl.grid, wl.basis, wl.pusher, precision=V.VP_FP32)
+    assert sim.plan()["state_is_s"] == 1
+    sim.set_f(I.make_f0(wl).astype(np.float32))
+    for k in range(4):
+        sim.step(3)
+        sim.get_f(np.float32)
+        sim.moments()
+        sim.state_ptr()
+    f = sim.get_f(np.float32)
+    h = sim.field_history()
+    sim.close()
+    assert np.array_equal(f, f_plain)
+    assert np.array_equal(h, h_plain)
