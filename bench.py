@@ -418,7 +418,8 @@ def main():
     N = g.nodes
     f0 = I.make_f0(wl).astype(np.float32)
     stream = torch.cuda.Stream()
-    # working set of a step: two state buffers and the solve scratch. Below twice the L2, each
+    # working set of a step: two state buffers, and the deposit buffer of the separate-x-pass plan
+    # (counted either way here). Below twice the L2, each
     # timed step runs after an L2 flush; above it, the steps run back to back.
     working = 3 * 4 * N
     cold = working < 2 * L2_BYTES
@@ -625,8 +626,10 @@ def main():
                                   f"({2 * L2_BYTES / 2**20:.0f} MiB written) before every timed step, "
                                   f"the step timed by its own events"
                                   if cold else
-                                  f"inputs larger than L2 (two {4 * N / 2**20:.0f} MiB state buffers + "
-                                  f"{4 * N / 2**20:.0f} MiB solve scratch)")},
+                                  f"inputs larger than L2 (workspace {plan['workspace_bytes'] / 2**20:.0f} MiB: "
+                                  f"two {4 * N / 2**20:.0f} MiB state buffers"
+                                  + (f" + the {4 * N / 2**20:.0f} MiB deposit between the tile and row passes"
+                                     if xpass else "") + ")")},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
                 "late_window": late,
                 "gpu_launches": launches_per_step * args.steps, "extra": extra}
