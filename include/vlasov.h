@@ -164,8 +164,15 @@ vp_status vp_create(const vp_grid *grid, int32_t basis, const vp_pusher *pusher,
  * (no staging copy); otherwise it is copied to the device first.
  * Resets step, tau, lost mass and A = A0. */
 vp_status vp_set_f(vp_sim *sim, const void *host, int32_t dtype, size_t n);
-/* Same from device memory (device-to-device on the sim's stream). */
+/* Same from device memory (device-to-device on the sim's stream; ordered on that stream only:
+ * whatever produced dev on another stream must have finished). */
 vp_status vp_set_f_device(vp_sim *sim, const void *dev, int32_t dtype, size_t n);
+/* vp_set_f without waiting: the weights (dtype = the sim's precision, else VP_ERR_ARG) are
+ * copied to the device by the copy engine on the sim's stream, then Lambda_p is applied; the
+ * call returns at once. The host buffer must stay valid and unchanged until the stream has
+ * passed the copy (vp_sync, or any later synchronising call). Pinned memory makes the copy
+ * truly asynchronous, and lets simulations on other streams overlap their transfers with it. */
+vp_status vp_set_f_async(vp_sim *sim, const void *host, int32_t dtype, size_t n);
 
 /* Advance n steps: push + deposit (+ Lambda^{-1}) (+ FEL bunching and field). Asynchronous. */
 vp_status vp_step(vp_sim *sim, int32_t n);
@@ -185,6 +192,11 @@ vp_status vp_step_profiled(vp_sim *sim, int32_t n, double *phase_ms, int32_t nph
  * weights into it in place; otherwise they are staged on the device and copied. */
 vp_status vp_get_f(vp_sim *sim, void *host, int32_t dtype, size_t n);
 vp_status vp_get_f_device(vp_sim *sim, void *dev, int32_t dtype, size_t n);
+/* vp_get_f without waiting: the weights (dtype = the sim's precision, else VP_ERR_ARG) are
+ * formed on the device and copied to host by the copy engine on the sim's stream; the call
+ * returns at once, and the host buffer holds them once the stream has passed the copy
+ * (vp_sync). Device-side errors (non-finite weights) are reported by that vp_sync. */
+vp_status vp_get_f_async(vp_sim *sim, void *host, int32_t dtype, size_t n);
 
 /* FP64 reductions over the current weights; synchronises. */
 vp_status vp_moments(vp_sim *sim, vp_moments_t *out);

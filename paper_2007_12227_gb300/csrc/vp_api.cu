@@ -582,14 +582,25 @@ vp_status do_steps(vp_sim *s, int n, cudaEvent_t *ev = nullptr)
     return VP_OK;
 }
 
+// the initial state block, written by a kernel from its argument (no host buffer to keep alive, so
+// nothing here waits for the stream)
+struct StateBlock {
+    double v[ST_NSTATE];
+};
+__global__ void put_state_kernel(double *dst, StateBlock b)
+{
+    for (int k = threadIdx.x; k < ST_NSTATE; k += blockDim.x) dst[k] = b.v[k];
+}
+
 vp_status reset_state(vp_sim *s, const void *w)
 {
     const Plan &P = s->P;
-    memset(s->host_state, 0, sizeof(s->host_state));
-    s->host_state[ST_A_RE] = s->a0_re;
-    s->host_state[ST_A_IM] = s->a0_im;
-    VP_CUDA(s, cudaMemcpyAsync(s->ws + P.L.state, s->host_state, sizeof(s->host_state),
-                               cudaMemcpyHostToDevice, s->stream));
+    StateBlock b;
+    memset(&b, 0, sizeof(b));
+    b.v[ST_A_RE] = s->a0_re;
+    b.v[ST_A_IM] = s->a0_im;
+    put_state_kernel<<<1, 32, 0, s->stream>>>(s->ptr<double>(P.L.state), b);
+    VP_CUDA(s, cudaGetLastError());
     VP_CUDA(s, cudaMemsetAsync(s->ws + P.L.lost, 0, P.nlost * sizeof(double), s->stream));
     VP_CUDA(s, cudaMemsetAsync(s->ws + P.L.err, 0, sizeof(unsigned), s->stream));
     if (P.kernel == VP_KERNEL_FUSED) VP_CUDA(s, cudaMemsetAsync(s->ws + P.L.ticket, 0, sizeof(int), s->stream));
@@ -599,8 +610,6 @@ vp_status reset_state(vp_sim *s, const void *w)
                                               : fel_bunching<float>(s, w, 1);
         if (st != VP_OK) return st;
     }
-    // the host copy above reads host_state: finish it before the struct is reused
-    VP_CUDA(s, cudaStreamSynchronize(s->stream));
     return VP_OK;
 }
 
@@ -853,8 +862,11 @@ static void *host_device_ptr(const void *p, size_t align)
     return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
-static vp_status set_f_common(vp_sim *s, const void *src, int32_t dtype, size_t n, bool device)
+enum class Xfer { host, device, host_async };
+
+static vp_status set_f_common(vp_sim *s, const void *src, int32_t dtype, size_t n, Xfer mode)
 {
+    const bool device = mode == Xfer::device, async = mode == Xfer::host_async;
     if (!s) return VP_ERR_ARG;
     const Plan &P = s->P;
     const size_t N = (size_t)P.g.nx * P.g.np;
@@ -864,8 +876,12 @@ static vp_status set_f_common(vp_sim *s, const void *src, int32_t dtype, size_t 
     // the weights go to the state buffer, or to the idle buffer f1 when the state is s = Lambda_p w
     void *dst = P.state_s ? s->f(1) : s->f(0);
     const size_t szs = P.precision == VP_FP64 ? 8 : 4;
-    // pinned host weights and the state s = Lambda_p w: Lambda_p reads them in place
-    void *hdev = (!device && dtype == P.precision && P.state_s) ? host_device_ptr(src, szs) : nullptr;
+    if (async && dtype != P.precision)
+        return fail(s->msg, VP_ERR_ARG, "set_f_async: the weights must have the simulation's dtype");
+    // pinned host weights and the state s = Lambda_p w: Lambda_p reads them in place (the
+    // asynchronous call copies them with the copy engine instead, which overlaps other streams'
+    // transfers in the opposite direction)
+    void *hdev = (!device && !async && dtype == P.precision && P.state_s) ? host_device_ptr(src, szs) : nullptr;
     if (hdev) {
         dst = hdev;
     } else if (dtype == P.precision) {
@@ -915,19 +931,25 @@ static vp_status set_f_common(vp_sim *s, const void *src, int32_t dtype, size_t 
         VP_CUDA(s, launch_tile_max(static_cast<const float *>(s->f(0)), s->ptr<float>(P.L.smax), P.g.nx,
                                    P.g.np, P.tx, P.tp, P.ntx, P.ntp, s->ptr<unsigned>(P.L.err),
                                    s->stream));
-    // the caller owns the host buffer again once set_f returns
-    if (hdev) VP_CUDA(s, cudaStreamSynchronize(s->stream));
+    // the caller owns the host buffer again once vp_set_f returns; the asynchronous form leaves it
+    // to the caller's vp_sync
+    if (mode == Xfer::host) VP_CUDA(s, cudaStreamSynchronize(s->stream));
     return VP_OK;
 }
 
 vp_status vp_set_f(vp_sim *s, const void *host, int32_t dtype, size_t n)
 {
-    return set_f_common(s, host, dtype, n, false);
+    return set_f_common(s, host, dtype, n, Xfer::host);
+}
+
+vp_status vp_set_f_async(vp_sim *s, const void *host, int32_t dtype, size_t n)
+{
+    return set_f_common(s, host, dtype, n, Xfer::host_async);
 }
 
 vp_status vp_set_f_device(vp_sim *s, const void *dev, int32_t dtype, size_t n)
 {
-    return set_f_common(s, dev, dtype, n, true);
+    return set_f_common(s, dev, dtype, n, Xfer::device);
 }
 
 vp_status vp_step(vp_sim *s, int32_t n)
@@ -975,18 +997,22 @@ vp_status vp_step_profiled(vp_sim *s, int32_t n, double *phase_ms, int32_t nphas
     return st;
 }
 
-static vp_status get_f_common(vp_sim *s, void *dstp, int32_t dtype, size_t n, bool device)
+static vp_status get_f_common(vp_sim *s, void *dstp, int32_t dtype, size_t n, Xfer mode)
 {
+    const bool device = mode == Xfer::device, async = mode == Xfer::host_async;
     if (!s) return VP_ERR_ARG;
     const Plan &P = s->P;
     const size_t N = (size_t)P.g.nx * P.g.np;
     if (!dstp || n != N || (dtype != VP_FP32 && dtype != VP_FP64))
         return fail(s->msg, VP_ERR_ARG, "get_f: need room for %zu values of dtype FP32/FP64", N);
     if (!s->f_set) return fail(s->msg, VP_ERR_STATE, "vp_get_f before vp_set_f");
+    if (async && dtype != P.precision)
+        return fail(s->msg, VP_ERR_ARG, "get_f_async: the weights must have the simulation's dtype");
     const void *src = nullptr;
     const size_t szs = P.precision == VP_FP64 ? 8 : 4;
     // a pinned host buffer and the state s = Lambda_p w: the p solve writes the weights in place
-    void *hdev = (!device && dtype == P.precision && P.state_s) ? host_device_ptr(dstp, szs) : nullptr;
+    // (the asynchronous call solves into device memory and copies with the copy engine)
+    void *hdev = (!device && !async && dtype == P.precision && P.state_s) ? host_device_ptr(dstp, szs) : nullptr;
     {
         vp_status st = P.precision == VP_FP64 ? weights_of_state<double>(s, &src, hdev)
                                               : weights_of_state<float>(s, &src, hdev);
@@ -1019,18 +1045,23 @@ static vp_status get_f_common(vp_sim *s, void *dstp, int32_t dtype, size_t n, bo
             for (size_t k = 0; k < N; ++k) o[k] = (float)in[k];
         }
     }
-    if (device) return VP_OK;
+    if (mode != Xfer::host) return VP_OK;
     return check_flags(s);
 }
 
 vp_status vp_get_f(vp_sim *s, void *host, int32_t dtype, size_t n)
 {
-    return get_f_common(s, host, dtype, n, false);
+    return get_f_common(s, host, dtype, n, Xfer::host);
+}
+
+vp_status vp_get_f_async(vp_sim *s, void *host, int32_t dtype, size_t n)
+{
+    return get_f_common(s, host, dtype, n, Xfer::host_async);
 }
 
 vp_status vp_get_f_device(vp_sim *s, void *dev, int32_t dtype, size_t n)
 {
-    return get_f_common(s, dev, dtype, n, true);
+    return get_f_common(s, dev, dtype, n, Xfer::device);
 }
 
 vp_status vp_moments(vp_sim *s, vp_moments_t *out)

@@ -106,10 +106,12 @@ _SIGNATURES = [
                             C.c_void_p, C.c_size_t, C.POINTER(C.c_void_p)]),
     ("vp_set_f", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_size_t]),
     ("vp_set_f_device", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_size_t]),
+    ("vp_set_f_async", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_size_t]),
     ("vp_step", C.c_int, [C.c_void_p, C.c_int32]),
     ("vp_step_profiled", C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_double), C.c_int32]),
     ("vp_get_f", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_size_t]),
     ("vp_get_f_device", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_size_t]),
+    ("vp_get_f_async", C.c_int, [C.c_void_p, C.c_void_p, C.c_int32, C.c_size_t]),
     ("vp_moments", C.c_int, [C.c_void_p, C.POINTER(vp_moments_t)]),
     ("vp_field_history", C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.c_size_t,
                                    C.POINTER(C.c_size_t)]),
@@ -237,11 +239,17 @@ class Sim:
             t = f.contiguous()
             import torch
             dt = VP_FP64 if t.dtype == torch.float64 else VP_FP32
+            # the library reads t on the sim's stream: whatever wrote it on torch's stream finishes first
+            torch.cuda.current_stream(t.device).synchronize()
             _check(lib().vp_set_f_device(self.h, C.c_void_p(t.data_ptr()), dt, t.numel()), self.h)
             self._keep = t
 
     def set_f_host_ptr(self, ptr: int, dtype: int):
         _check(lib().vp_set_f(self.h, C.c_void_p(ptr), dtype, self.n), self.h)
+
+    def set_f_async_ptr(self, ptr: int, dtype: int):
+        """vp_set_f_async: returns at once; keep the host buffer unchanged until sync()."""
+        _check(lib().vp_set_f_async(self.h, C.c_void_p(ptr), dtype, self.n), self.h)
 
     def step(self, n=1):
         _check(lib().vp_step(self.h, int(n)), self.h)
@@ -260,6 +268,10 @@ class Sim:
 
     def get_f_host_ptr(self, ptr: int, dtype: int):
         _check(lib().vp_get_f(self.h, C.c_void_p(ptr), dtype, self.n), self.h)
+
+    def get_f_async_ptr(self, ptr: int, dtype: int):
+        """vp_get_f_async: returns at once; the host buffer holds the weights after sync()."""
+        _check(lib().vp_get_f_async(self.h, C.c_void_p(ptr), dtype, self.n), self.h)
 
     def get_f_device(self, out):
         import torch

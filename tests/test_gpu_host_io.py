@@ -93,3 +93,48 @@ def test_misaligned_pinned_buffer_is_staged():
     got = np.frombuffer(raw.numpy()[off:off + 4 * n].tobytes(), dtype=np.float32).reshape(f0.shape)
     sim.close()
     assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("kernel", [V.VP_KERNEL_AUTO, V.VP_KERNEL_FUSED_XPASS])
+@pytest.mark.parametrize("precision", [I.FP32, I.FP64])
+def test_async_transfers_match_the_synchronous_calls(kernel, precision):
+    """vp_set_f_async / vp_get_f_async (copy engine on the sim's stream, no wait) give what
+    vp_set_f / vp_get_f give; two simulations on two streams interleaved from one thread, as the
+    benchmark's end-to-end loop runs them, give what one simulation gives. FP32 sums integer
+    window cells: the same bits. FP64 deposits with floating-point atomics, whose order varies
+    from run to run: equal to within a few roundings."""
+    wl = pendulum(1000, 650, precision)
+    npt = np.float32 if precision == I.FP32 else np.float64
+    tdt = torch.float32 if precision == I.FP32 else torch.float64
+    f0 = I.make_f0(wl).astype(npt)
+    ref = V.Sim(wl.grid, wl.basis, wl.pusher, precision=precision, kernel=kernel)
+    ref.set_f(f0)
+    ref.step(2)
+    want = ref.get_f(npt)
+    ref.close()
+    pipes = []
+    for _ in range(2):
+        sim = V.Sim(wl.grid, wl.basis, wl.pusher, precision=precision, kernel=kernel,
+                    stream=torch.cuda.Stream())
+        hin = torch.from_numpy(f0.reshape(-1)).pin_memory()
+        hout = torch.zeros(f0.size, dtype=tdt).pin_memory()
+        pipes.append((sim, hin, hout))
+    for k in range(4):
+        sim, hin, hout = pipes[k % 2]
+        if k >= 2:
+            sim.sync()
+        sim.set_f_async_ptr(hin.data_ptr(), precision)
+        sim.step(2)
+        sim.get_f_async_ptr(hout.data_ptr(), precision)
+    for sim, _, hout in pipes:
+        sim.sync()
+        got = hout.numpy().reshape(want.shape)
+        if precision == I.FP32:
+            assert np.array_equal(got, want)
+        else:
+            assert np.max(np.abs(got - want)) <= 1e-13 * np.max(np.abs(want))
+        other = V.VP_FP64 if precision == I.FP32 else V.VP_FP32
+        with pytest.raises(V.VlasovError) as ei:
+            sim.get_f_async_ptr(hout.data_ptr(), other)
+        assert ei.value.status == V.VP_ERR_ARG
+        sim.close()
