@@ -635,6 +635,32 @@ def main():
                            "warm_l2_ms_per_step": warm}
         fsim.close()
 
+    if not args.skip_extra and rank == 0 and args.workload == "pendulum":
+        # the same mesh with the lumped projection (Lambda replaced by its row sum: the step is the
+        # deposit alone, no solves), on the autotuner's plan for it
+        ltuned = V.autotune([wl], projection=V.VP_PROJ_LUMPED, stream=stream)[0]
+        lsim = V.Sim(g, wl.basis, wl.pusher, precision=V.VP_FP32, projection=V.VP_PROJ_LUMPED,
+                     kernel=ltuned["kernel"], tile_x=ltuned["tile_x"], tile_p=ltuned["tile_p"], stream=stream)
+        lsim.set_f(f0)
+        lsim.step(10)
+        lsim.sync()
+        nl = 200
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lsim.step(nl)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        lms = e0.elapsed_time(e1) / nl
+        lplan = lsim.plan()
+        extra[wl.name + "_lumped"] = {"node_updates_per_s": N / (lms * 1e-3), "ms_per_step": lms,
+                                      "steps_timed": nl, "tile": [lplan["tile_x"], lplan["tile_p"]],
+                                      "launches_per_step": lplan["launches_per_step"],
+                                      "algorithmic_gbs": 8 * N / (lms * 1e-3) / 1e9,
+                                      "frac_of_hbm_peak": 8 * N / (lms * 1e-3) / 1e9 / peak,
+                                      "l2": "steps back to back (inputs larger than L2)"}
+        lsim.close()
+
     if not args.skip_extra and rank == 0 and not args.skip_batch:
         extra["batch_256"] = bench_batch(V, torch, stream, args.batch_steps)
     if not args.skip_extra and rank == 0 and not args.skip_serve:

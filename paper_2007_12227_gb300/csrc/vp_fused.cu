@@ -998,22 +998,35 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
                 for (int a = 0; a < N; ++a) rg.acc[q][a] = T(0);
             T wx[N], wy[N];
             if (!GAL) {
-                const T *sp = src + (size_t)ja * nx;
-                if (rows_cached) {
-#pragma unroll 2
-                    for (int jj = ja; jj <= jb; ++jj, sp += nx) {
-                        int m, n;
-                        node_taps<T, BASIS, UTERM, true>(cc, srow[jj], colrel, jj - W.WP0, *sp * qs, m, n, wx,
-                                                         wy);
-                        ring_add<T, N, 1>(win, W, rg, m, n, wx, wy, lost);
+                // the deposit alone: each chunk of kC source rows is loaded first (all of its loads
+                // in flight, kept in the column buffer), then walked upwards
+                T *gc = gcol + tid;
+                const int nth = blockDim.x;
+                for (int c_lo = ja; c_lo <= jb; c_lo += kC) {
+                    const int c_hi = min(jb, c_lo + kC - 1);
+                    const T *sp = src + (size_t)c_lo * nx;
+                    if (c_hi - c_lo + 1 == kC) {
+#pragma unroll
+                        for (int k = 0; k < kC; ++k) gc[k * nth] = __ldg(sp + (size_t)k * nx);
+                    } else {
+                        for (int k = 0; k <= c_hi - c_lo; ++k) gc[k * nth] = __ldg(sp + (size_t)k * nx);
                     }
-                } else {
-#pragma unroll 2
-                    for (int jj = ja; jj <= jb; ++jj, sp += nx) {
-                        int m, n;
-                        node_taps<T, BASIS, UTERM, false>(cc, A.row[jj], colrel, jj - W.WP0, *sp * qs, m, n,
-                                                          wx, wy);
-                        ring_add<T, N, 1>(win, W, rg, m, n, wx, wy, lost);
+                    if (rows_cached) {
+#pragma unroll 1
+                        for (int r = c_lo; r <= c_hi; ++r) {
+                            int m, n;
+                            node_taps<T, BASIS, UTERM, true>(cc, srow[r], colrel, r - W.WP0,
+                                                             gc[(r - c_lo) * nth] * qs, m, n, wx, wy);
+                            ring_add<T, N, 1>(win, W, rg, m, n, wx, wy, lost);
+                        }
+                    } else {
+#pragma unroll 1
+                        for (int r = c_lo; r <= c_hi; ++r) {
+                            int m, n;
+                            node_taps<T, BASIS, UTERM, false>(cc, A.row[r], colrel, r - W.WP0,
+                                                              gc[(r - c_lo) * nth] * qs, m, n, wx, wy);
+                            ring_add<T, N, 1>(win, W, rg, m, n, wx, wy, lost);
+                        }
                     }
                 }
                 ring_final<T, N>(win, W, rg, lost);

@@ -328,3 +328,13 @@ def test_pendulum_8192_fp32_cubic_at_the_autotuned_tile():
     tuned = V.autotune([wl])[0]
     got, st, _, _, _ = run_pair(wl, 2, kernel=tuned["kernel"], tile=(tuned["tile_x"], tuned["tile_p"]))
     check(got, st.w, I.FP32)
+
+
+def test_pendulum_8192_fp32_cubic_lumped_at_the_autotuned_tile():
+    """The benchmark's lumped line: the 8192^2 pendulum with Lambda replaced by its row sum (the
+    deposit alone), on the plan the autotuner picks for it, one step against the oracle."""
+    wl = I.pendulum_8192_fp32_cubic()
+    tuned = V.autotune([wl], projection=I.PROJ_LUMPED)[0]
+    got, st, _, _, _ = run_pair(wl, 1, kernel=tuned["kernel"], tile=(tuned["tile_x"], tuned["tile_p"]),
+                                projection=I.PROJ_LUMPED)
+    check(got, st.w, I.FP32)
