@@ -62,6 +62,9 @@ def parse():
     ap.add_argument("--kernel", default="auto", choices=["auto", "fused", "xpass"],
                     help="step plan: the planner's, the one-pass kernel, or the one-pass tile with a "
                          "separate x-solve row pass")
+    ap.add_argument("--projection", default="galerkin", choices=["galerkin", "lumped"],
+                    help="the timed workload's treatment of Lambda: the Galerkin solve (the headline) "
+                         "or its row sum (the deposit alone)")
     ap.add_argument("--e2e-pipes", type=int, default=3,
                     help="simulations (each on its own stream) the end-to-end loop interleaves")
     ap.add_argument("--skip-late", action="store_true",
@@ -416,6 +419,7 @@ def main():
     wl = workload(args.size, args.workload)
     kernel = {"auto": V.VP_KERNEL_AUTO, "fused": V.VP_KERNEL_FUSED,
               "xpass": V.VP_KERNEL_FUSED_XPASS}[args.kernel]
+    proj = V.VP_PROJ_LUMPED if args.projection == "lumped" else V.VP_PROJ_GALERKIN
     g = wl.grid
     N = g.nodes
     f0 = I.make_f0(wl).astype(np.float32)
@@ -433,11 +437,12 @@ def main():
         tuned = {"tile_x": tx, "tile_p": tp, "candidates": 0, "ms_per_step": None,
                  "default_ms_per_step": None}
     else:
-        tuned = V.autotune([wl], kernel=kernel, stream=stream)[0]
+        tuned = V.autotune([wl], projection=proj, kernel=kernel, stream=stream)[0]
     t_tune = time.perf_counter() - t_tune
     # the tuner's plan: its kernel (the one-pass kernel or its separate-x-pass form) and shape
     plan_kernel = tuned.get("kernel", kernel) if not args.tile else kernel
-    sim = V.Sim(g, wl.basis, wl.pusher, precision=V.VP_FP32, kernel=plan_kernel, tile_x=tuned["tile_x"],
+    sim = V.Sim(g, wl.basis, wl.pusher, precision=V.VP_FP32, projection=proj, kernel=plan_kernel,
+                tile_x=tuned["tile_x"],
                 tile_p=tuned["tile_p"], stream=stream)
     sim.set_f(f0)
     sim.step(args.warmup)
@@ -492,6 +497,8 @@ def main():
                     "fel_4096x2048_fp32_cubic": "step_fused_fel_4096x2048.md"}.get(wl.name, "none.md")
     if xpass:
         step_profile = step_profile.replace("step_fused_", "step_fused_xpass_")
+    if args.projection == "lumped":
+        step_profile = step_profile.replace("step_fused_", "step_fused_lumped_")
     kernel_files = {"push_deposit": (step_profile, FUSED_SOURCES),
                     "lambda_inv_x": ("xsolve_rows_pendulum_8192.md", FUSED_SOURCES) if xpass else
                                     ("filter_x_pendulum_8192.md", ["paper_2007_12227_gb300/csrc/vp_filter.cu"]),
@@ -566,7 +573,7 @@ def main():
         wall_seq = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
         pipes = [(sim, host_in, host_out)]
         for _ in range(npipe - 1):
-            pipes.append((V.Sim(g, wl.basis, wl.pusher, precision=V.VP_FP32, kernel=plan_kernel,
+            pipes.append((V.Sim(g, wl.basis, wl.pusher, precision=V.VP_FP32, projection=proj, kernel=plan_kernel,
                                 tile_x=tuned["tile_x"], tile_p=tuned["tile_p"], stream=torch.cuda.Stream()),
                           torch.from_numpy(f0).pin_memory(), torch.empty_like(host_in).pin_memory()))
 
@@ -635,7 +642,7 @@ def main():
                            "warm_l2_ms_per_step": warm}
         fsim.close()
 
-    if not args.skip_extra and rank == 0 and args.workload == "pendulum":
+    if not args.skip_extra and rank == 0 and args.workload == "pendulum" and args.projection == "galerkin":
         # the same mesh with the lumped projection (Lambda replaced by its row sum: the step is the
         # deposit alone, no solves), on the autotuner's plan for it
         ltuned = V.autotune([wl], projection=V.VP_PROJ_LUMPED, stream=stream)[0]
@@ -682,7 +689,7 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32", "data": "synthetic",
                 "config": {"workload": wl.name, "mesh": f"{g.nx}x{g.np}", "dt": wl.pusher.dt,
-                           "basis": "cubic_bspline_galerkin", "parallelism": f"replicas{ws}",
+                           "basis": f"cubic_bspline_{args.projection}", "parallelism": f"replicas{ws}",
                            "tile": [plan["tile_x"], plan["tile_p"]],
                            "plan": ("one-pass tile kernel without the x solve + exact x-solve row pass"
                                     if xpass else "one-pass step kernel"),
