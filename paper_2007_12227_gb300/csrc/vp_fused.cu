@@ -660,6 +660,44 @@ __device__ __forceinline__ void solve_row_x_exact(const T *row, int lane, T *v, 
 
 }  // namespace
 
+// The window's own cells in weight units into the destination rows: one warp per row, FP32 rows
+// with 16-byte loads of the fixed-point cells and 16-byte stores where the destination row allows.
+// MAX: track max|value| in om (the stored state's per-tile maximum) and flag non-finite values
+// (FP64 cells; FP32 cells are integers times a finite scale).
+template <typename T, bool MAX>
+__device__ __forceinline__ void store_window_rows(const T *win, const WinGeom &W, T *dst, int nx, int P0,
+                                                  int X0, int TXe, int TPe, int G, int Gp, T iq, int warp,
+                                                  int nwarps, int lane, float &om, bool &bad)
+{
+    for (int rr = warp; rr < TPe; rr += nwarps) {
+        const T *row = win + (size_t)(rr + Gp) * W.ws + G;
+        T *drow = dst + (size_t)(P0 + rr) * nx + X0;
+        int c0 = 0;
+        if constexpr (sizeof(T) == 4) {
+            if ((reinterpret_cast<uintptr_t>(drow) & 15) == 0) {
+                const int n4 = TXe >> 2;
+                const int4 *r4 = reinterpret_cast<const int4 *>(row);
+                float4 *d4 = reinterpret_cast<float4 *>(drow);
+                for (int c4 = lane; c4 < n4; c4 += 32) {
+                    const int4 q = r4[c4];
+                    const float4 o = make_float4((float)q.x * iq, (float)q.y * iq, (float)q.z * iq, (float)q.w * iq);
+                    d4[c4] = o;
+                    if (MAX) om = fmaxf(om, fmaxf(fmaxf(fabsf(o.x), fabsf(o.y)), fmaxf(fabsf(o.z), fabsf(o.w))));
+                }
+                c0 = n4 << 2;
+            }
+        }
+        for (int c = c0 + lane; c < TXe; c += 32) {
+            const T v = wget(row + c, iq);
+            drow[c] = v;
+            if (MAX) {
+                om = fmaxf(om, fabsf((float)v));
+                bad |= !isfinite(v);
+            }
+        }
+    }
+}
+
 // Lambda_x solve of the tile's window rows (one warp per row) and the tile store.
 template <typename T, int KX>
 __device__ __forceinline__ void gal_rows(T *win, const WinGeom &W, T *dst, int L, bool full, int D,
@@ -1146,27 +1184,9 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
     float om = 0.f;   // FP32: max|s'| of the stored outputs
     double pw = 0.0, pc = 0.0, ps = 0.0;
     if (GAL && A.xpass) {
-        // separate x pass: store the deposit r = Delta^T w of the own columns in weight units
-        // (one warp per row; 16-byte stores where the row allows); the row pass solves Lambda_x,
-        // records max|s'| per tile and checks the outputs
-        for (int rr = warp; rr < TPe; rr += nwarps) {
-            const T *row = win + (size_t)(rr + Gp) * W.ws + G;
-            T *drow = A.dst + (size_t)(P0 + rr) * nx + X0;
-            int c0 = 0;
-            if constexpr (sizeof(T) == 4) {
-                if ((reinterpret_cast<uintptr_t>(drow) & 15) == 0) {
-                    const int n4 = TXe >> 2;
-                    const int4 *r4 = reinterpret_cast<const int4 *>(row);
-                    float4 *d4 = reinterpret_cast<float4 *>(drow);
-                    for (int c4 = lane; c4 < n4; c4 += 32) {
-                        const int4 q = r4[c4];
-                        d4[c4] = make_float4((float)q.x * iq, (float)q.y * iq, (float)q.z * iq, (float)q.w * iq);
-                    }
-                    c0 = n4 << 2;
-                }
-            }
-            for (int c = c0 + lane; c < TXe; c += 32) drow[c] = wget(row + c, iq);
-        }
+        // separate x pass: store the deposit r = Delta^T w of the own columns in weight units; the
+        // row pass solves Lambda_x, records max|s'| per tile and checks the outputs
+        store_window_rows<T, false>(win, W, A.dst, nx, P0, X0, TXe, TPe, G, Gp, iq, warp, nwarps, lane, om, bad);
     } else if (GAL) {
         const int L = full ? nx : TXe + 2 * D;
         const bool f32 = sizeof(T) == 4;
@@ -1180,13 +1200,8 @@ __device__ __forceinline__ void fused_tile(const FusedArgs<T> &A, const int tile
                                warp, nwarps, lane, bad, gcol, GRows<T>::value * blockDim.x, sh, sl, iq,
                                om);
     } else {
-        for (int k = tid; k < TXe * TPe; k += blockDim.x) {
-            const int rr = k / TXe, c = k - rr * TXe;
-            const T v = wget(win + (size_t)(rr + Gp) * W.ws + G + c, iq);
-            A.dst[(size_t)(P0 + rr) * nx + X0 + c] = v;
-            om = fmaxf(om, fabsf((float)v));
-            bad |= !isfinite(v);
-        }
+        // no solve: the deposit is the new state (its max|w| sets the next step's window scale)
+        store_window_rows<T, true>(win, W, A.dst, nx, P0, X0, TXe, TPe, G, Gp, iq, warp, nwarps, lane, om, bad);
     }
     if (want_part) {
         // FEL: column sums of w over the tile (Galerkin: sum_j w_ij = sum_j sigma_j s_ij; with a
